@@ -1,0 +1,131 @@
+/* hsc.h -- C ABI of the GB300 HSC-extension selected-inversion library (libhsc.so).
+ *
+ * Computes, for many energies E in one call, selected entries of
+ *     G^r(E) = A(E)^{-1},   A(E) = (E + i*eta) I - H - Sigma^r(E)          (Eq. 1)
+ *     G^<(E) = G^r(E) Sigma^<(E) G^r(E)^dagger                             (Eq. 2)
+ * by nested-dissection selected inversion: Algorithm 1 (HSC, G^r) and Algorithm 2 (HSC-extension,
+ * G^<) over the binary cluster tree of Section 2.2. Selected entries are the diagonal and any
+ * (a, b) inside the filled pattern of the ordered factorisation; every pair with H_ab != 0 is in it.
+ *
+ * Conventions
+ *   - H is complex symmetric (H = H^T), given in CSR over n unknowns; the algorithms use transposes,
+ *     not adjoints (Eq. 3 and Algorithm 1 rely on A = A^T).
+ *   - Unknown u of site s and orbital o is u = s*orb + o. Contacts are sets of sites; the contact
+ *     unknowns are listed contact after contact, site after site, orbital after orbital, and the
+ *     self-energy arrays are indexed in that order ("contact slots").
+ *   - Sigma^r and Sigma^< are diagonal on the contact unknowns (Section 3.1.1, SPARSE self-energy).
+ *   - Complex numbers are interleaved (re, im) doubles. All outputs are in user (CSR) order.
+ *   - Every call returns an hsc_status; no exception crosses the ABI; hsc_last_error() gives text.
+ *   - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef HSC_H
+#define HSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsc_ctx* hsc_t;
+typedef struct { double re, im; } hsc_c128;
+
+typedef enum {
+  HSC_OK = 0,
+  HSC_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, index out of range)  */
+  HSC_ERR_NOT_SYMMETRIC = 2,  /* H != H^T                                                       */
+  HSC_ERR_STATE = 3,          /* call out of order (solve before analyze)                        */
+  HSC_ERR_SINGULAR = 4,       /* zero pivot in a cluster block (only possible with eta = 0)      */
+  HSC_ERR_NOT_SELECTED = 5,   /* requested pair outside the filled pattern                       */
+  HSC_ERR_OOM = 6,            /* device or host allocation failed                                */
+  HSC_ERR_CUDA = 7,           /* CUDA runtime error (message in hsc_last_error)                  */
+  HSC_ERR_TIMEOUT = 8         /* a bounded device-side wait expired                             */
+} hsc_status;
+
+typedef enum { HSC_FP64 = 0, HSC_MIXED = 1 } hsc_precision;
+
+typedef struct {
+  int32_t n_clusters;       /* clusters in the tree                                         */
+  int32_t n_heights;        /* upward stages (leaves are height 0)                          */
+  int32_t n_depths;         /* downward stages (root is depth 0)                            */
+  int32_t max_n;            /* largest cluster (unknowns)                                   */
+  int32_t max_m;            /* largest update set |U_i| (unknowns)                          */
+  int32_t n_lesser;         /* clusters whose subtree touches a contact                     */
+  int64_t n_unknowns;
+  double flops_gr;          /* model: real flops per energy for G^r (complex MAC = 8)        */
+  double flops_gl;          /* model: real flops per energy for G^<                          */
+  int64_t bytes_per_energy; /* device workspace per energy of a solve                       */
+} hsc_tree_stats;
+
+typedef struct {
+  int32_t n, m;             /* own unknowns, update-set unknowns                            */
+  int32_t parent;           /* -1 for the root                                              */
+  int32_t child[2];         /* -1 where absent                                              */
+  int32_t height, depth;
+  int32_t lesser;           /* 1 if the subtree holds a contact unknown                     */
+} hsc_cluster_info;
+
+/* hsc_create -- copy the device description into a new handle (no GPU work).
+ *   n            number of unknowns (multiple of orb)
+ *   orb          orbitals per site
+ *   rowptr,col,val  H in CSR over unknowns: rowptr[n+1] (int64), col[nnz] (int32), val[nnz];
+ *                 host memory, read only during the call (the handle keeps its own copy)
+ *   n_contacts, contact_ptr[n_contacts+1], contact_sites[...]  site sets of the contacts (host)
+ *   grid_dims    optional {Nx, Ny, Nz} (site = (x*Ny + y)*Nz + z): geometric nested dissection;
+ *                NULL selects breadth-first level-set bisection of the site graph.
+ * Errors: HSC_ERR_ARG (sizes, indices), HSC_ERR_NOT_SYMMETRIC (H != H^T), HSC_ERR_OOM.
+ * On error *out is set to NULL. Cite: Eq. 1 (H, Sigma^r), Section 3.1 (cuboid grids). */
+int hsc_create(hsc_t* out, int64_t n, int32_t orb,
+               const int64_t* rowptr, const int32_t* col, const hsc_c128* val,
+               int32_t n_contacts, const int64_t* contact_ptr, const int32_t* contact_sites,
+               const int32_t* grid_dims);
+
+/* hsc_analyze -- build the cluster tree (Section 2.2, multilevel nested dissection), the update
+ *   sets, the assembly/gather maps and the operation-count model. Host only; no GPU work.
+ *   leaf_max: geometric ND stops when every extent of a box is <= leaf_max sites; graph ND stops
+ *   at leaf_max^3 sites. stats may be NULL. Errors: HSC_ERR_ARG, HSC_ERR_OOM. */
+int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats);
+
+/* hsc_cluster -- describe cluster i (postorder id, root = n_clusters-1) after hsc_analyze.
+ *   own/upd: optional host arrays of at least n / m int32 entries receiving the user-order unknowns
+ *   of the cluster and of its update set U_i (ascending in the cluster ordering).
+ * Errors: HSC_ERR_STATE, HSC_ERR_ARG. */
+int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* own, int32_t* upd);
+
+/* hsc_solve -- selected G^r and G^< at n_E energies (Algorithms 1 and 2).
+ *   E[n_E]                energies (eV); eta (eV) > 0 recommended (eta = 0 may be singular)
+ *   sigma_r[n_E][n_cs]    diagonal Sigma^r on the n_cs contact slots, per energy
+ *   sigma_less[n_E][n_cs] diagonal Sigma^< per energy, or NULL: G^< work and outputs are skipped
+ *   precision             HSC_FP64 (complex128 throughout) or HSC_MIXED
+ *   n_req, req_pairs[n_req][2]  user-order unknown pairs (a, b) whose G^r_ab (and G^<_ab) are
+ *                         returned; every pair must be in the filled pattern
+ *   diag_gr[n_E][n]       out: G^r_uu;            diag_gl[n_E][n] out: G^<_uu (ignored if
+ *                         sigma_less is NULL);    req_gr[n_E][n_req], req_gl[n_E][n_req] out (may be
+ *                         NULL when n_req = 0)
+ *   cuda_stream           cudaStream_t to run on (NULL: the legacy default stream)
+ *   io_on_device          0: E, sigma_*, req_pairs and all outputs are host memory (the call copies
+ *                         them in and out and returns after the results are on the host);
+ *                         1: E, sigma_* and outputs are device memory (req_pairs stays on the host)
+ *                         and the call returns once the work is enqueued on cuda_stream.
+ * The handle owns its device workspace (allocated on the first solve, grown as needed, freed by
+ * hsc_destroy). Energies are processed in waves that fit the workspace budget
+ * (HSC_WORKSPACE_GB, default 64 GB).
+ * Errors: HSC_ERR_STATE (no analyze), HSC_ERR_ARG, HSC_ERR_NOT_SELECTED, HSC_ERR_OOM,
+ *   HSC_ERR_CUDA, HSC_ERR_SINGULAR (reported after the fact from a device flag). */
+int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
+              const hsc_c128* sigma_r, const hsc_c128* sigma_less, int32_t precision,
+              int32_t n_req, const int32_t* req_pairs,
+              hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl,
+              void* cuda_stream, int32_t io_on_device);
+
+/* hsc_last_error -- text of the last failure on this handle ("" if none); valid until the next
+ * call on the handle. Accepts NULL (returns the last global error, e.g. from hsc_create). */
+const char* hsc_last_error(hsc_t h);
+
+/* hsc_destroy -- free the handle and its device workspace. NULL is accepted. */
+int hsc_destroy(hsc_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSC_H */

@@ -1,0 +1,178 @@
+// Host half of the C ABI: handle creation, validation, analysis and tree queries (no GPU work).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+#include <new>
+#include <string>
+
+#include "ctx.h"
+
+static thread_local std::string g_err;
+
+int hsc_fail(hsc_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+extern "C" int hsc_create(hsc_t* out, int64_t n, int32_t orb, const int64_t* rowptr,
+                          const int32_t* col, const hsc_c128* val, int32_t n_contacts,
+                          const int64_t* contact_ptr, const int32_t* contact_sites,
+                          const int32_t* grid_dims) {
+  if (!out) return hsc_fail(nullptr, HSC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || orb <= 0 || n % orb) return hsc_fail(nullptr, HSC_ERR_ARG, "n must be a positive multiple of orb");
+  if (!rowptr || !col || !val) return hsc_fail(nullptr, HSC_ERR_ARG, "CSR pointer is NULL");
+  if (n_contacts < 0 || (n_contacts > 0 && (!contact_ptr || !contact_sites)))
+    return hsc_fail(nullptr, HSC_ERR_ARG, "bad contact arrays");
+  if (rowptr[0] != 0) return hsc_fail(nullptr, HSC_ERR_ARG, "rowptr[0] != 0");
+  for (int64_t u = 0; u < n; ++u)
+    if (rowptr[u + 1] < rowptr[u]) return hsc_fail(nullptr, HSC_ERR_ARG, "rowptr not monotone");
+  const int64_t nnz = rowptr[n];
+  for (int64_t e = 0; e < nnz; ++e)
+    if (col[e] < 0 || col[e] >= n) return hsc_fail(nullptr, HSC_ERR_ARG, "column index out of range");
+  // complex symmetry H = H^T (Eq. 3: the block LDL^T form needs A = A^T): the sorted entry list
+  // (row, col, value) must equal the sorted list of (col, row, value)
+  {
+    struct Ent { int64_t r, c; double re, im; };
+    std::vector<Ent> a, b;
+    try {
+      a.reserve(nnz);
+      b.reserve(nnz);
+    } catch (...) {
+      return hsc_fail(nullptr, HSC_ERR_OOM, "out of host memory");
+    }
+    for (int64_t u = 0; u < n; ++u)
+      for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        a.push_back({u, col[e], val[e].re, val[e].im});
+        b.push_back({col[e], u, val[e].re, val[e].im});
+      }
+    auto lt = [](const Ent& x, const Ent& y) {
+      if (x.r != y.r) return x.r < y.r;
+      if (x.c != y.c) return x.c < y.c;
+      if (x.re != y.re) return x.re < y.re;
+      return x.im < y.im;
+    };
+    std::sort(a.begin(), a.end(), lt);
+    std::sort(b.begin(), b.end(), lt);
+    for (int64_t k = 0; k < nnz; ++k)
+      if (a[k].r != b[k].r || a[k].c != b[k].c || a[k].re != b[k].re || a[k].im != b[k].im)
+        return hsc_fail(nullptr, HSC_ERR_NOT_SYMMETRIC, "H is not complex symmetric (H != H^T)");
+  }
+  int64_t n_sites = n / orb, ncu = 0;
+  if (n_contacts > 0) {
+    if (contact_ptr[0] != 0) return hsc_fail(nullptr, HSC_ERR_ARG, "contact_ptr[0] != 0");
+    for (int c = 0; c < n_contacts; ++c) {
+      if (contact_ptr[c + 1] < contact_ptr[c]) return hsc_fail(nullptr, HSC_ERR_ARG, "contact_ptr not monotone");
+      for (int64_t k = contact_ptr[c]; k < contact_ptr[c + 1]; ++k)
+        if (contact_sites[k] < 0 || contact_sites[k] >= n_sites)
+          return hsc_fail(nullptr, HSC_ERR_ARG, "contact site out of range");
+    }
+    ncu = contact_ptr[n_contacts] * orb;
+  }
+  if (grid_dims) {
+    if (grid_dims[0] <= 0 || grid_dims[1] <= 0 || grid_dims[2] <= 0 ||
+        (int64_t)grid_dims[0] * grid_dims[1] * grid_dims[2] != n_sites)
+      return hsc_fail(nullptr, HSC_ERR_ARG, "grid_dims do not match n/orb");
+  }
+  hsc_ctx* h = new (std::nothrow) hsc_ctx();
+  if (!h) return hsc_fail(nullptr, HSC_ERR_OOM, "out of host memory");
+  try {
+    h->n = n;
+    h->orb = orb;
+    h->rowptr.assign(rowptr, rowptr + n + 1);
+    h->col.assign(col, col + nnz);
+    h->val.assign(val, val + nnz);
+    h->n_contacts = n_contacts;
+    if (n_contacts > 0) {
+      h->contact_ptr.assign(contact_ptr, contact_ptr + n_contacts + 1);
+      h->contact_sites.assign(contact_sites, contact_sites + contact_ptr[n_contacts]);
+    } else {
+      h->contact_ptr.assign(1, 0);
+    }
+    h->n_contact_unknowns = ncu;
+    if (grid_dims) std::memcpy(h->dims, grid_dims, sizeof(h->dims));
+  } catch (...) {
+    delete h;
+    return hsc_fail(nullptr, HSC_ERR_OOM, "out of host memory");
+  }
+  *out = h;
+  g_err.clear();
+  return HSC_OK;
+}
+
+extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  h->analyzed = false;
+  hsc::Input in;
+  in.n = h->n;
+  in.orb = h->orb;
+  in.rowptr = h->rowptr.data();
+  in.col = h->col.data();
+  in.n_contacts = h->n_contacts;
+  in.contact_ptr = h->contact_ptr.data();
+  in.contact_sites = h->contact_sites.data();
+  std::memcpy(in.dims, h->dims, sizeof(in.dims));
+  std::string e;
+  try {
+    e = hsc::analyze(in, leaf_max, h->plan);
+  } catch (const std::bad_alloc&) {
+    return hsc_fail(h, HSC_ERR_OOM, "out of host memory in analyze");
+  }
+  if (!e.empty()) return hsc_fail(h, HSC_ERR_ARG, e);
+  const hsc::Plan& P = h->plan;
+  hsc_tree_stats s{};
+  s.n_clusters = (int32_t)P.cl.size();
+  s.n_heights = (int32_t)P.by_height.size();
+  s.n_depths = (int32_t)P.by_depth.size();
+  for (const auto& c : P.cl) {
+    s.max_n = std::max<int32_t>(s.max_n, (int32_t)c.n);
+    s.max_m = std::max<int32_t>(s.max_m, (int32_t)c.m);
+    s.n_lesser += c.lesser ? 1 : 0;
+  }
+  s.n_unknowns = h->n;
+  s.flops_gr = P.flops_gr;
+  s.flops_gl = P.flops_gl;
+  // per energy: F, G, P, L (aug) and S, LS (square) in complex128
+  s.bytes_per_energy = (4 * P.tot_aug + 2 * P.tot_sq) * 16;
+  h->stats = s;
+  if (stats) *stats = s;
+  h->analyzed = true;
+  h->err.clear();
+  return HSC_OK;
+}
+
+extern "C" int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* own, int32_t* upd) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  const hsc::Plan& P = h->plan;
+  if (i < 0 || i >= (int32_t)P.cl.size()) return hsc_fail(h, HSC_ERR_ARG, "cluster index out of range");
+  const hsc::Cluster& c = P.cl[i];
+  if (info) {
+    info->n = (int32_t)c.n;
+    info->m = (int32_t)c.m;
+    info->parent = c.parent;
+    info->child[0] = c.child[0];
+    info->child[1] = c.child[1];
+    info->height = c.height;
+    info->depth = c.depth;
+    info->lesser = c.lesser ? 1 : 0;
+  }
+  const int orb = h->orb;
+  if (own)
+    for (size_t k = 0; k < c.sites.size(); ++k)
+      for (int o = 0; o < orb; ++o) own[k * orb + o] = c.sites[k] * orb + o;
+  if (upd)
+    for (size_t k = 0; k < c.usites.size(); ++k)
+      for (int o = 0; o < orb; ++o) upd[k * orb + o] = c.usites[k] * orb + o;
+  return HSC_OK;
+}
+
+extern "C" const char* hsc_last_error(hsc_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+extern "C" int hsc_destroy(hsc_t h) {
+  if (!h) return HSC_OK;
+  hsc::device_state_free(h->dev);
+  delete h;
+  return HSC_OK;
+}

@@ -1,0 +1,32 @@
+// Handle state shared by the host API (api.cpp) and the device driver (solve.cu).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/hsc.h"
+#include "plan.h"
+
+namespace hsc {
+struct DeviceState;                 // defined in solve.cu
+void device_state_free(DeviceState*);
+}  // namespace hsc
+
+struct hsc_ctx {
+  int64_t n = 0;
+  int orb = 1;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<hsc_c128> val;
+  int n_contacts = 0;
+  std::vector<int64_t> contact_ptr;
+  std::vector<int32_t> contact_sites;
+  int64_t n_contact_unknowns = 0;
+  int dims[3] = {0, 0, 0};
+  bool analyzed = false;
+  hsc::Plan plan;
+  hsc_tree_stats stats{};
+  std::string err;
+  hsc::DeviceState* dev = nullptr;
+};
+
+int hsc_fail(hsc_ctx* h, int code, const std::string& msg);

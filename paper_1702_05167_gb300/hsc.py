@@ -1,0 +1,187 @@
+"""Thin ctypes binding of libhsc (include/hsc.h): same entry-point names, argument marshalling only.
+
+Every step of the solve runs inside libhsc's CUDA kernels; this module only converts numpy arrays or
+torch tensors to pointers. If the shared library is missing it raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HSC_OK, HSC_ERR_ARG, HSC_ERR_NOT_SYMMETRIC, HSC_ERR_STATE, HSC_ERR_SINGULAR, \
+    HSC_ERR_NOT_SELECTED, HSC_ERR_OOM, HSC_ERR_CUDA, HSC_ERR_TIMEOUT = range(9)
+HSC_FP64, HSC_MIXED = 0, 1
+STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR_STATE",
+          4: "HSC_ERR_SINGULAR", 5: "HSC_ERR_NOT_SELECTED", 6: "HSC_ERR_OOM", 7: "HSC_ERR_CUDA",
+          8: "HSC_ERR_TIMEOUT"}
+
+EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_last_error",
+           "hsc_destroy"]
+
+
+class hsc_tree_stats(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int32), ("n_heights", ctypes.c_int32),
+                ("n_depths", ctypes.c_int32), ("max_n", ctypes.c_int32), ("max_m", ctypes.c_int32),
+                ("n_lesser", ctypes.c_int32), ("n_unknowns", ctypes.c_int64),
+                ("flops_gr", ctypes.c_double), ("flops_gl", ctypes.c_double),
+                ("bytes_per_energy", ctypes.c_int64)]
+
+
+class hsc_cluster_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("parent", ctypes.c_int32),
+                ("child", ctypes.c_int32 * 2), ("height", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("lesser", ctypes.c_int32)]
+
+
+class HSCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def lib_path():
+    return os.environ.get("HSC_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                     "libhsc.so")
+
+
+def load():
+    """Load libhsc.so (built in-tree by __graft_entry__.build()); raise if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libhsc.so not found at {p}: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(p)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.hsc_create.argtypes = [ctypes.POINTER(vp), i64, i32, vp, vp, vp, i32, vp, vp, vp]
+    L.hsc_analyze.argtypes = [vp, i32, ctypes.POINTER(hsc_tree_stats)]
+    L.hsc_cluster.argtypes = [vp, i32, ctypes.POINTER(hsc_cluster_info), vp, vp]
+    L.hsc_solve.argtypes = [vp, i64, vp, dp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, i32]
+    L.hsc_last_error.argtypes = [vp]
+    L.hsc_last_error.restype = ctypes.c_char_p
+    L.hsc_destroy.argtypes = [vp]
+    for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_destroy"):
+        getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(h, code):
+    if code != HSC_OK:
+        msg = load().hsc_last_error(h).decode(errors="replace")
+        raise HSCError(code, msg)
+
+
+def hsc_create(n, orb, rowptr, col, val, contact_ptr, contact_sites, grid_dims=None):
+    L = load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.complex128)
+    contact_ptr = np.ascontiguousarray(contact_ptr, dtype=np.int64)
+    contact_sites = np.ascontiguousarray(contact_sites, dtype=np.int32)
+    dims = None if grid_dims is None else np.ascontiguousarray(grid_dims, dtype=np.int32)
+    h = ctypes.c_void_p()
+    code = L.hsc_create(ctypes.byref(h), int(n), int(orb), _ptr(rowptr), _ptr(col), _ptr(val),
+                        len(contact_ptr) - 1, _ptr(contact_ptr), _ptr(contact_sites), _ptr(dims))
+    _check(None, code)
+    return h
+
+
+def hsc_analyze(h, leaf_max):
+    st = hsc_tree_stats()
+    _check(h, load().hsc_analyze(h, int(leaf_max), ctypes.byref(st)))
+    return st
+
+
+def hsc_cluster(h, i, want_sets=True):
+    info = hsc_cluster_info()
+    _check(h, load().hsc_cluster(h, int(i), ctypes.byref(info), None, None))
+    own = upd = None
+    if want_sets:
+        own = np.empty(info.n, dtype=np.int32)
+        upd = np.empty(info.m, dtype=np.int32)
+        _check(h, load().hsc_cluster(h, int(i), None, _ptr(own), _ptr(upd)))
+    return info, own, upd
+
+
+def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, diag_gl, req_gr,
+              req_gl, stream=None, io_on_device=False):
+    """Marshal buffers to hsc_solve. Buffers are numpy (host) or torch (device) arrays; complex128
+    arrays are passed as interleaved doubles."""
+    n_E = int(E.shape[0])
+    pairs = None
+    n_req = 0
+    if req_pairs is not None and len(req_pairs):
+        pairs = np.ascontiguousarray(req_pairs, dtype=np.int32)
+        n_req = pairs.shape[0]
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    code = load().hsc_solve(h, n_E, _ptr(E), float(eta), _ptr(sigma_r), _ptr(sigma_less),
+                            int(precision), n_req, _ptr(pairs), _ptr(diag_gr), _ptr(diag_gl),
+                            _ptr(req_gr), _ptr(req_gl), s, 1 if io_on_device else 0)
+    _check(h, code)
+
+
+def hsc_last_error(h=None):
+    return load().hsc_last_error(h).decode(errors="replace")
+
+
+def hsc_destroy(h):
+    if h is not None:
+        load().hsc_destroy(h)
+
+
+class Solver:
+    """Convenience owner of one handle for a workloads.Device (create + analyze)."""
+
+    def __init__(self, dev, leaf_max, geometric=True):
+        self.dev = dev
+        self.h = hsc_create(dev.n, dev.orb, dev.rowptr, dev.col, dev.val, dev.contact_ptr,
+                            dev.contact_sites, dev.dims if geometric else None)
+        self.stats = hsc_analyze(self.h, leaf_max)
+
+    def solve(self, E, eta, sigma_r, sigma_less=None, precision=HSC_FP64, pairs=None):
+        """Host-memory solve; returns (diag_gr, diag_gl, req_gr, req_gl) as numpy arrays."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        n_E, n = len(E), self.dev.n
+        sigma_r = np.ascontiguousarray(sigma_r, dtype=np.complex128)
+        if sigma_less is not None:
+            sigma_less = np.ascontiguousarray(sigma_less, dtype=np.complex128)
+        n_req = 0 if pairs is None else len(pairs)
+        dgr = np.zeros((n_E, n), dtype=np.complex128)
+        dgl = np.zeros((n_E, n), dtype=np.complex128) if sigma_less is not None else None
+        rgr = np.zeros((n_E, n_req), dtype=np.complex128) if n_req else None
+        rgl = np.zeros((n_E, n_req), dtype=np.complex128) if (n_req and sigma_less is not None) else None
+        hsc_solve(self.h, E, eta, sigma_r, sigma_less, precision, pairs, dgr, dgl, rgr, rgl)
+        return dgr, dgl, rgr, rgl
+
+    def close(self):
+        hsc_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass
