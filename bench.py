@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark: energy points per second for diag(G^r, G^<) on the 32^3 tight-binding grid.
+
+Workload (one "step"): one hsc_solve over the 64-energy grid linspace(-5.5, 5.5, 64) of the
+32x32x32 simple-cubic device (W = 1 eV disorder, wide-band contacts on x = 0 and x = 31, eta = 1e-6,
+leaves <= 8^3), complex128 throughout, returning diag G^r, diag G^< and the G^r / G^< coupling
+blocks between planes x = 15 and x = 16. Synthetic, seeded inputs (workloads.mid()).
+
+Arms:
+  default          the CUDA path through the C ABI; `value` times device-resident inputs/outputs,
+                   `e2e` times the host-buffer call (host<->device copies inside the timed region).
+  --impl reference the CPU oracle (recursive Green's function sweep, complex128) on the host cores,
+                   each step one energy of the same workload (a bounded sample).
+
+Multi-GPU (torchrun, one process per GPU): every rank solves its own 64-energy grid (interleaved
+sub-grids), no data-path collective; value = energies of all ranks / max-over-ranks time
+(weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy pts/s for diag(G^r,G^<) on 32^3 grid"
+UNIT = "energy_points/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="hsc", choices=["hsc", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank, ws):
+    from paper_1702_05167_gb300 import workloads as W
+    cfg = W.mid()
+    E = cfg["energies"]
+    if ws > 1:   # interleaved sub-grids: rank r shifts the grid by r/ws of a spacing
+        E = E + (E[1] - E[0]) * rank / ws
+    cfg["energies"] = E
+    return cfg
+
+
+def cpu_oracle_energy(cfg, k):
+    """One energy of the workload by the RGF oracle; returns seconds."""
+    from oracle import rgf
+    from paper_1702_05167_gb300 import workloads as W
+    dev = cfg["dev"]
+    sr, sl = W.self_energies(dev, 1, cfg["f"])
+    H = dev.to_scipy()
+    t0 = time.perf_counter()
+    rgf.sweep(H, dev.dims[1] * dev.dims[2] * dev.orb, cfg["energies"][k], cfg["eta"],
+              dev.contact_unknowns(), sr[0], sl[0], coupling_layers=(15,))
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    cfg = workload(0, 1)
+    ks = [20, 43, 7, 56, 31, 12, 50, 2]
+    for w in range(args.warmup):
+        cpu_oracle_energy(cfg, ks[w % len(ks)])
+    ts = [cpu_oracle_energy(cfg, ks[(args.warmup + s) % len(ks)]) for s in range(args.steps)]
+    tot = sum(ts)
+    value = args.steps / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "cubic_32x32x32_64E (W=1 eV, eta=1e-6, contacts x=0/x=31)",
+                       "oracle": "RGF sweep along x, complex128, numpy/OpenBLAS",
+                       "step": "one energy of the 64-energy grid (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} energies of the 64-energy grid, 1 per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_hsc(args):
+    import torch
+    from paper_1702_05167_gb300 import hsc, workloads as W
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dvc = torch.device("cuda", local)
+    cfg = workload(rank, ws)
+    dev = cfg["dev"]
+    E = cfg["energies"]
+    nE = len(E)
+    sr, sl = W.self_energies(dev, nE, cfg["f"])
+    pairs = cfg["pairs"]
+    solver = hsc.Solver(dev, cfg["leaf"])
+    st = solver.stats
+    h = solver.h
+    n = dev.n
+    npair = len(pairs)
+
+    tE = torch.from_numpy(E).to(dvc)
+    tsr = torch.from_numpy(sr.view(np.float64)).to(dvc)
+    tsl = torch.from_numpy(sl.view(np.float64)).to(dvc)
+    ogr = torch.empty((nE, 2 * n), dtype=torch.float64, device=dvc)
+    ogl = torch.empty_like(ogr)
+    pgr = torch.empty((nE, 2 * npair), dtype=torch.float64, device=dvc)
+    pgl = torch.empty_like(pgr)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        hsc.hsc_solve(h, tE, cfg["eta"], tsr, tsl, hsc.HSC_FP64, pairs, ogr, ogl, pgr, pgl,
+                      stream=stream.cuda_stream, io_on_device=True)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    hsc.hsc_profile(h, True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = hsc.hsc_profile_read(h)
+    hsc.hsc_profile(h, False)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dvc)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nE * args.steps * ws / (ms / 1000.0)
+    launches = int(sum(p["launches"] for p in prof))
+
+    # ---- end to end through the host-buffer C-ABI call (copies inside the timed region) ----
+    e2e = None
+    if not args.no_e2e:
+        hE = torch.from_numpy(E.copy()).pin_memory().numpy()
+        hsr = torch.from_numpy(sr.view(np.float64).copy()).pin_memory().numpy().view(np.complex128)
+        hsl = torch.from_numpy(sl.view(np.float64).copy()).pin_memory().numpy().view(np.complex128)
+        hgr = torch.empty((nE, 2 * n), dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        hgl = torch.empty((nE, 2 * n), dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        hpr = torch.empty((nE, 2 * npair), dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        hpl = torch.empty((nE, 2 * npair), dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        hsc.hsc_solve(h, hE, cfg["eta"], hsr, hsl, hsc.HSC_FP64, pairs, hgr, hgl, hpr, hpl)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            hsc.hsc_solve(h, hE, cfg["eta"], hsr, hsl, hsc.HSC_FP64, pairs, hgr, hgl, hpr, hpl)
+        torch.cuda.synchronize()
+        barrier()
+        es = time.perf_counter() - e0
+        if ws > 1:
+            t = torch.tensor([es], dtype=torch.float64, device=dvc)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            es = float(t.item())
+        e2e = {"value": nE * args.steps * ws / es, "unit": UNIT,
+               "h2d_bytes_per_step": int(hE.nbytes + hsr.nbytes + hsl.nbytes + 8 * npair),
+               "d2h_bytes_per_step": int(hgr.nbytes + hgl.nbytes + hpr.nbytes + hpl.nbytes)}
+
+    # ---- roofline of the dominant kernel class (complex GEMM on the FP64 tensor pipe) ----
+    dmma, dfma = hsc.hsc_device_fp64_peaks()
+    g = next(p for p in prof if p["name"] == "gemm_z_dmma")
+    tot_ms = sum(p["ms"] for p in prof)
+    achieved = g["flops"] / (g["ms"] / 1000.0) / 1e12 if g["ms"] > 0 else 0.0
+    peak = dmma / 1000.0
+    roof = {"kernel": "k_gemm_z (grouped complex128 GEMM, mma.sync m8n8k4 f64)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "peak_source": "FP64 tensor-pipe throughput probe (hsc_device_fp64_peaks) on this GPU "
+                           "in this run; MEASURED_PEAKS.json has no FP64 figure",
+            "scalar_fp64_peak_tflops": dfma / 1000.0,
+            "share_of_device_time": g["ms"] / tot_ms if tot_ms > 0 else None,
+            "launches": g["timed"], "avg_launch_ms": g["ms"] / max(g["timed"], 1)}
+    kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                           "share": round(p["ms"] / tot_ms, 4) if tot_ms else None}
+               for p in prof}
+    model_tflops = (st.flops_gr + st.flops_gl) * nE * args.steps / (ms / 1000.0) / 1e12
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t = cpu_oracle_energy(cfg, 20)
+        cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "1 energy (E index 20) of the 64-energy grid, RGF sweep, complex128"}
+
+    solver.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+                "config": {"workload": "cubic_32x32x32_64E", "grid": [32, 32, 32],
+                           "energies_per_gpu": nE, "eta": cfg["eta"], "leaf_max": cfg["leaf"],
+                           "precision": "complex128 (HSC_FP64)", "io": "device-resident",
+                           "clusters": st.n_clusters,
+                           "l2": "working set ~%.0f GB >> L2 (no flush needed)" % (st.bytes_per_energy * nE / 1e9),
+                           "parallelism": f"energy-sharded x{ws}"},
+                "model_tflops": model_tflops, "model_gflop_per_energy": (st.flops_gr + st.flops_gl) / 1e9,
+                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_hsc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,12 +104,13 @@ int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* own, int32_
  *                         NULL when n_req = 0)
  *   cuda_stream           cudaStream_t to run on (NULL: the legacy default stream)
  *   io_on_device          0: E, sigma_*, req_pairs and all outputs are host memory (the call copies
- *                         them in and out and returns after the results are on the host);
- *                         1: E, sigma_* and outputs are device memory (req_pairs stays on the host)
- *                         and the call returns once the work is enqueued on cuda_stream.
+ *                         them in and out through device staging buffers);
+ *                         1: E, sigma_* and outputs are device memory (req_pairs stays on the host).
+ *                         In both modes the call synchronises cuda_stream before returning, to
+ *                         read the device error flags (singular pivot, internal map error).
  * The handle owns its device workspace (allocated on the first solve, grown as needed, freed by
  * hsc_destroy). Energies are processed in waves that fit the workspace budget
- * (HSC_WORKSPACE_GB, default 64 GB).
+ * (HSC_WORKSPACE_GB caps it; default 85% of the free device memory).
  * Errors: HSC_ERR_STATE (no analyze), HSC_ERR_ARG, HSC_ERR_NOT_SELECTED, HSC_ERR_OOM,
  *   HSC_ERR_CUDA, HSC_ERR_SINGULAR (reported after the fact from a device flag). */
 int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
@@ -117,6 +118,36 @@ int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
               int32_t n_req, const int32_t* req_pairs,
               hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl,
               void* cuda_stream, int32_t io_on_device);
+
+/* Kernel-class statistics of the launches hsc_solve made since the last hsc_profile call.
+ *   launches  kernel launches of the class (counted whether or not timing is enabled)
+ *   timed     launches bracketed by CUDA events (only while timing is enabled)
+ *   ms        sum of the event-measured device durations of those launches (milliseconds)
+ *   flops     algorithmic real flops of those launches (complex multiply-add = 8)
+ *   bytes     algorithmic bytes moved by those launches (memory-bound classes only) */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  int64_t timed;
+  double ms;
+  double flops;
+  double bytes;
+} hsc_kernel_stat;
+
+/* hsc_profile -- reset the kernel statistics; enable = 1 additionally brackets every kernel launch
+ *   of subsequent hsc_solve calls with CUDA events on the solve's stream (device-side timing;
+ *   a small host overhead per launch), enable = 0 stops the timing. No GPU work. */
+int hsc_profile(hsc_t h, int32_t enable);
+
+/* hsc_profile_read -- per-class statistics (host array of cap >= *n_out entries; call with
+ *   out = NULL to query *n_out). Waits for the recorded events. Errors: HSC_ERR_ARG, HSC_ERR_CUDA. */
+int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int32_t* n_out);
+
+/* hsc_device_fp64_peaks -- measure, on the current device, the throughput of the FP64 tensor pipe
+ *   (mma.sync m8n8k4 f64, which the complex128 GEMMs use) and of scalar FP64 FMA, in GFLOP/s
+ *   (best of three ~10 ms launches). These are the roofline denominators of the complex128 path.
+ *   Errors: HSC_ERR_ARG, HSC_ERR_CUDA, HSC_ERR_OOM. */
+int hsc_device_fp64_peaks(double* dmma_gflops, double* dfma_gflops);
 
 /* hsc_last_error -- text of the last failure on this handle ("" if none); valid until the next
  * call on the handle. Accepts NULL (returns the last global error, e.g. from hsc_create). */

@@ -1,0 +1,75 @@
+// Device-side shared definitions for the HSC kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hsc {
+
+typedef double2 c64;   // complex128 (x = re, y = im)
+typedef float2 c32;    // complex64
+
+__host__ __device__ inline c64 cmul(c64 a, c64 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline c64 cadd(c64 a, c64 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline c64 csub(c64 a, c64 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline c64 cconj(c64 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline c64 cneg(c64 a) { return make_double2(-a.x, -a.y); }
+
+// One problem of a grouped GEMM:  C = alpha * op(A) op(B) + beta * D   (D rows in [zr0, zr1) are
+// treated as zero). Offsets are element offsets inside the per-energy slice of each operand array.
+struct GemmProb {
+  int M, N, K;
+  int lda, ldb, ldc, ldd;
+  int zr0, zr1;
+  int use_d;          // 0: drop the beta * D term for this problem
+  int tiles_n;        // ceil(N / BN)
+  int tile_start;     // first tile index of this problem in the flattened tile space
+  int64_t a, b, c, d; // element offsets
+};
+
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_H = 3 };   // none, transpose, conjugate, adjoint
+
+struct GemmArgs {
+  const GemmProb* probs;
+  int nprob;
+  int total_tiles;
+  const void* A; int64_t a_es;    // base pointers and per-energy strides (elements)
+  const void* B; int64_t b_es;
+  void* C; int64_t c_es;
+  const void* D; int64_t d_es;
+  double ar, ai, br, bi;          // alpha, beta
+  int opa, opb;
+  double flops;                   // algorithmic real flops per energy (host bookkeeping)
+};
+
+// launchers (gemm_f64.cu)
+cudaError_t gemm_z(const GemmArgs& g, int n_energy, cudaStream_t s);
+
+// Gauss-Jordan inversion problem: n x n matrix at element offset `off` (row stride ld) of a
+// per-energy array; pivots at piv_off of the per-energy pivot array; panel copy M (n x nb, row
+// stride nb) and row block R (nb x n, row stride n) at mt_off / rt_off of per-energy temporaries.
+struct GJProb {
+  int n, ld;
+  int64_t off, piv_off, mt_off, rt_off;
+};
+
+// Per-level description of the clusters for the element-wise kernels.
+struct LevelCluster {
+  int n, m, lesser;
+  int child[2];          // cluster ids or -1
+  int64_t aug, sq;       // per-energy offsets of the cluster's aug (n x (n+m)) / square (m x m) blocks
+  int64_t x;             // offset of X = D^{-1} A_iU (n x m)
+  int64_t tt, tz, tn;    // level-temporary offsets: n x m, m x m, n x (n+m)
+  int64_t map0, map1;    // child front maps
+  int64_t h0, h1;        // H-entry range
+  int64_t own0;          // own-unknown range start (own_contact, pivots)
+  int64_t u0, pm0;       // update-set gather arrays
+  int nseg, depth;
+  int64_t elem_start;    // flattened element prefix inside the level (kernel-specific)
+};
+
+struct ClusterGlobal {   // per-cluster data needed when another cluster reads this one's blocks
+  int n, m, depth, lesser;
+  int64_t aug, sq;
+};
+
+}  // namespace hsc

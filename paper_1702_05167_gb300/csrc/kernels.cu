@@ -1,0 +1,420 @@
+// Element-wise and factorisation kernels of the HSC / HSC-extension path (complex128):
+//   * front assembly by gather (extend-add of the children's Schur and lesser updates),
+//   * insertion of A(E) = (E + i eta) I - H - Sigma^r and of Sigma^< into the fronts (Eq. 1-2),
+//   * blocked Gauss-Jordan inversion of the cluster blocks A_ii with partial pivoting inside the
+//     block (the D_i^{-1} of Eq. 3 / Algorithm 1),
+//   * the anti-Hermitian completion of the lesser fold (Algorithm 2),
+//   * gathers of G_UU and P_UU from the ancestors' stored blocks (Algorithms 1-2, downward pass),
+//   * scatter of diag G^r, diag G^< and requested entries to user order.
+#include "kernels.cuh"
+
+namespace hsc {
+namespace {
+
+__device__ __forceinline__ c64 crecip(c64 d) {
+  double s = d.x * d.x + d.y * d.y;
+  return make_double2(d.x / s, -d.y / s);
+}
+
+// ---- assembly -------------------------------------------------------------------------------
+
+__global__ void k_assemble(const LevelCluster* lc, int nl, int64_t total, const ClusterGlobal* cg,
+                           const int32_t* maps, c64* F, c64* S, c64* L, c64* LS, int64_t aug_es,
+                           int64_t sq_es, int ne, int do_lesser) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (lc[mid].elem_start <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const LevelCluster& C = lc[lo];
+    const int64_t n = C.n, m = C.m, idx = g - C.elem_start;
+    int64_t rpos, cpos, dst;
+    bool aug = idx < n * (n + m);
+    if (aug) {
+      rpos = idx / (n + m);
+      cpos = idx % (n + m);
+      dst = C.aug + idx;
+    } else {
+      int64_t j = idx - n * (n + m);
+      rpos = n + j / m;
+      cpos = n + j % m;
+      dst = C.sq + j;
+    }
+    int64_t src[2] = {-1, -1};
+    int les[2] = {0, 0};
+    for (int k = 0; k < 2; ++k) {
+      int c = C.child[k];
+      if (c < 0) continue;
+      const int32_t* mp = maps + (k == 0 ? C.map0 : C.map1);
+      int32_t a = mp[rpos], b = mp[cpos];
+      if (a >= 0 && b >= 0) {
+        src[k] = cg[c].sq + (int64_t)a * cg[c].m + b;
+        les[k] = cg[c].lesser;
+      }
+    }
+    const bool wl = do_lesser && C.lesser;
+    for (int e = 0; e < ne; ++e) {
+      c64 v = make_double2(0.0, 0.0), lv = make_double2(0.0, 0.0);
+      for (int k = 0; k < 2; ++k)
+        if (src[k] >= 0) {
+          v = cadd(v, S[e * sq_es + src[k]]);
+          if (wl && les[k]) lv = cadd(lv, LS[e * sq_es + src[k]]);
+        }
+      if (aug) {
+        F[e * aug_es + dst] = v;
+        if (wl) L[e * aug_es + dst] = lv;
+      } else {
+        S[e * sq_es + dst] = v;
+        if (wl) LS[e * sq_es + dst] = lv;
+      }
+    }
+  }
+}
+
+// F -= H on the original entries of each front (rows own, columns own or ancestors)
+__global__ void k_add_h(const LevelCluster* lc, const int32_t* h_rq, const int64_t* h_vi,
+                        const c64* hval, c64* F, int64_t aug_es, int ne) {
+  const LevelCluster& C = lc[blockIdx.y];
+  int64_t k = C.h0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= C.h1) return;
+  int64_t r = h_rq[2 * k], q = h_rq[2 * k + 1];
+  c64 h = hval[h_vi[k]];
+  int64_t dst = C.aug + r * (C.n + C.m) + q;
+  for (int e = 0; e < ne; ++e) {
+    atomicAdd(&F[e * aug_es + dst].x, -h.x);
+    atomicAdd(&F[e * aug_es + dst].y, -h.y);
+  }
+}
+
+// diagonal: (E + i eta) - Sigma^r on A, Sigma^< on the lesser front (Eq. 1-2)
+__global__ void k_add_diag(const LevelCluster* lc, const int32_t* own_contact, const double* E,
+                           double eta, const c64* sr, const c64* sl, int64_t ncs, c64* F, c64* L,
+                           int64_t aug_es, int ne) {
+  const LevelCluster& C = lc[blockIdx.y];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= C.n) return;
+  int32_t slot = own_contact[C.own0 + r];
+  int64_t dst = C.aug + (int64_t)r * (C.n + C.m) + r;
+  for (int e = 0; e < ne; ++e) {
+    c64 v = F[e * aug_es + dst];
+    v.x += E[e];
+    v.y += eta;
+    if (slot >= 0) v = csub(v, sr[e * ncs + slot]);
+    F[e * aug_es + dst] = v;
+    if (sl && C.lesser) {
+      c64 l = L[e * aug_es + dst];
+      if (slot >= 0) l = cadd(l, sl[e * ncs + slot]);
+      L[e * aug_es + dst] = l;
+    }
+  }
+}
+
+// ---- Gauss-Jordan -----------------------------------------------------------------------------
+
+constexpr int GJ_THREADS = 256;
+
+// Unblocked Gauss-Jordan on the panel columns [k0, k0+w) of every row, with the pivot of column j
+// chosen as the largest |re|+|im| among rows j..n-1 and the swap confined to the panel; then the
+// panel is moved to M (and zeroed in place) and the identity part of R is written.
+__global__ void __launch_bounds__(GJ_THREADS)
+k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_es, c64* Mt,
+           c64* Rt, int64_t t_es, int k0, int nb, int* flag) {
+  const GJProb P = probs[blockIdx.x];
+  const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
+  if (k0 >= n) return;
+  const int w = min(nb, n - k0);
+  c64* A = F + e * f_es + P.off;
+  int32_t* pv = piv + e * piv_es + P.piv_off;
+  __shared__ double s_v[GJ_THREADS / 32];
+  __shared__ int s_i[GJ_THREADS / 32];
+  __shared__ int s_p;
+  __shared__ c64 s_inv;
+  for (int j = k0; j < k0 + w; ++j) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = j + tid; r < n; r += GJ_THREADS) {
+      c64 v = A[(int64_t)r * ld + j];
+      double a = fabs(v.x) + fabs(v.y);
+      if (a > best) { best = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { s_v[tid >> 5] = best; s_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = s_v[0];
+      int ix = s_i[0];
+      for (int k = 1; k < GJ_THREADS / 32; ++k)
+        if (s_v[k] > b || (s_v[k] == b && s_i[k] < ix)) { b = s_v[k]; ix = s_i[k]; }
+      if (ix >= n) ix = j;
+      s_p = ix;
+      pv[j] = ix;
+      c64 d = A[(int64_t)ix * ld + j];
+      if (d.x == 0.0 && d.y == 0.0) {
+        atomicExch(flag, 1);
+        d = make_double2(1.0, 0.0);
+      }
+      s_inv = crecip(d);
+    }
+    __syncthreads();
+    const int p = s_p;
+    const c64 inv = s_inv;
+    if (p != j)
+      for (int c = tid; c < w; c += GJ_THREADS) {
+        c64 t = A[(int64_t)j * ld + k0 + c];
+        A[(int64_t)j * ld + k0 + c] = A[(int64_t)p * ld + k0 + c];
+        A[(int64_t)p * ld + k0 + c] = t;
+      }
+    __syncthreads();
+    for (int c = tid; c < w; c += GJ_THREADS) {
+      int64_t o = (int64_t)j * ld + k0 + c;
+      A[o] = (k0 + c == j) ? inv : cmul(A[o], inv);
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += GJ_THREADS) {
+      if (r == j) continue;
+      c64* row = A + (int64_t)r * ld;
+      const c64 f = row[j];
+      const c64* pr = A + (int64_t)j * ld;
+      for (int c = 0; c < w; ++c) {
+        if (k0 + c == j) continue;
+        row[k0 + c] = csub(row[k0 + c], cmul(f, pr[k0 + c]));
+      }
+      row[j] = cneg(cmul(f, inv));
+    }
+    __syncthreads();
+  }
+  c64* M = Mt + e * t_es + P.mt_off;
+  c64* R = Rt + e * t_es + P.rt_off;
+  for (int idx = tid; idx < n * w; idx += GJ_THREADS) {
+    int r = idx / w, c = idx % w;
+    M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
+    A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
+  }
+  for (int idx = tid; idx < w * w; idx += GJ_THREADS) {
+    int t = idx / w, c = idx % w;
+    R[(int64_t)t * n + k0 + c] = make_double2(t == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// apply the panel's row swaps to every column outside the panel and copy its pivot rows to R
+__global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32_t* piv,
+                          int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb) {
+  const GJProb P = probs[blockIdx.y];
+  const int e = blockIdx.z, n = P.n, ld = P.ld;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n || c >= n) return;
+  const int w = min(nb, n - k0);
+  if (c >= k0 && c < k0 + w) return;
+  c64* A = F + e * f_es + P.off;
+  const int32_t* pv = piv + e * piv_es + P.piv_off;
+  for (int j = k0; j < k0 + w; ++j) {
+    int p = pv[j];
+    if (p != j) {
+      c64 t = A[(int64_t)j * ld + c];
+      A[(int64_t)j * ld + c] = A[(int64_t)p * ld + c];
+      A[(int64_t)p * ld + c] = t;
+    }
+  }
+  c64* R = Rt + e * t_es + P.rt_off;
+  for (int t = 0; t < w; ++t) R[(int64_t)t * n + c] = A[(int64_t)(k0 + t) * ld + c];
+}
+
+// undo the row interchanges on the columns of the in-place inverse: A^{-1} = Y P
+__global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const int32_t* piv,
+                             int64_t piv_es) {
+  extern __shared__ unsigned char smem[];
+  const GJProb P = probs[blockIdx.x];
+  const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
+  c64* buf = reinterpret_cast<c64*>(smem);
+  int* idx = reinterpret_cast<int*>(buf + n);
+  c64* A = F + e * f_es + P.off;
+  const int32_t* pv = piv + e * piv_es + P.piv_off;
+  for (int c = tid; c < n; c += blockDim.x) idx[c] = c;
+  __syncthreads();
+  if (tid == 0)
+    for (int j = n - 1; j >= 0; --j) {
+      int p = pv[j];
+      if (p != j) { int t = idx[j]; idx[j] = idx[p]; idx[p] = t; }
+    }
+  __syncthreads();
+  for (int r = 0; r < n; ++r) {
+    c64* row = A + (int64_t)r * ld;
+    for (int c = tid; c < n; c += blockDim.x) buf[c] = row[c];
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) row[c] = buf[idx[c]];
+    __syncthreads();
+  }
+}
+
+// ---- lesser fold completion: LS += Z - Z^dagger --------------------------------------------
+
+__global__ void k_fold(const LevelCluster* lc, c64* LS, int64_t sq_es, const c64* Z, int64_t tz_es,
+                       int ne) {
+  const LevelCluster& C = lc[blockIdx.y];
+  const int64_t m = C.m;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!C.lesser || idx >= m * m) return;
+  int64_t a = idx / m, b = idx % m;
+  for (int e = 0; e < ne; ++e) {
+    c64 z = Z[e * tz_es + C.tz + a * m + b];
+    c64 zt = Z[e * tz_es + C.tz + b * m + a];
+    c64 v = LS[e * sq_es + C.sq + idx];
+    v.x += z.x - zt.x;
+    v.y += z.y + zt.y;
+    LS[e * sq_es + C.sq + idx] = v;
+  }
+}
+
+// ---- downward gathers --------------------------------------------------------------------------
+
+__global__ void k_gather(const LevelCluster* lc, const ClusterGlobal* cg, const int32_t* u_owner,
+                         const int32_t* u_local, const int32_t* u_seg, const int32_t* posmap,
+                         const c64* G, const c64* P, int64_t aug_es, c64* GUU, c64* PUU,
+                         int64_t tz_es, int ne, int* flag) {
+  const LevelCluster& C = lc[blockIdx.y];
+  const int64_t m = C.m;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  const int64_t k1 = idx / m, k2 = idx % m;
+  const int p1 = u_owner[C.u0 + k1], p2 = u_owner[C.u0 + k2];
+  const int64_t l1 = u_local[C.u0 + k1], l2 = u_local[C.u0 + k2];
+  int64_t src;
+  bool trans = false;
+  if (p1 == p2) {
+    src = cg[p1].aug + l1 * (cg[p1].n + cg[p1].m) + l2;
+  } else if (cg[p2].depth < cg[p1].depth) {
+    int32_t k = posmap[C.pm0 + k2 * C.nseg + u_seg[C.u0 + k1]];
+    if (k < 0) { atomicExch(flag, 2); return; }
+    src = cg[p1].aug + l1 * (cg[p1].n + cg[p1].m) + cg[p1].n + k;
+  } else {
+    int32_t k = posmap[C.pm0 + k1 * C.nseg + u_seg[C.u0 + k2]];
+    if (k < 0) { atomicExch(flag, 2); return; }
+    src = cg[p2].aug + l2 * (cg[p2].n + cg[p2].m) + cg[p2].n + k;
+    trans = true;
+  }
+  for (int e = 0; e < ne; ++e) {
+    GUU[e * tz_es + C.tz + idx] = G[e * aug_es + src];
+    if (PUU) {
+      c64 p = P[e * aug_es + src];
+      if (trans) p = make_double2(-p.x, p.y);   // P_ab = -conj(P_ba)
+      PUU[e * tz_es + C.tz + idx] = p;
+    }
+  }
+}
+
+// ---- outputs -----------------------------------------------------------------------------------
+
+__global__ void k_out_diag(const int64_t* doff, int64_t n, const c64* G, const c64* P,
+                           int64_t aug_es, c64* ogr, c64* ogl, int ne) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int64_t s = doff[u];
+  for (int e = 0; e < ne; ++e) {
+    ogr[e * n + u] = G[e * aug_es + s];
+    if (ogl) ogl[e * n + u] = P[e * aug_es + s];
+  }
+}
+
+__global__ void k_out_pairs(const int64_t* poff, int64_t npair, const c64* G, const c64* P,
+                            int64_t aug_es, c64* ogr, c64* ogl, int ne) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npair) return;
+  int64_t s = poff[k];
+  bool trans = s < 0;
+  if (trans) s = -s - 1;
+  for (int e = 0; e < ne; ++e) {
+    ogr[e * npair + k] = G[e * aug_es + s];
+    if (ogl) {
+      c64 p = P[e * aug_es + s];
+      if (trans) p = make_double2(-p.x, p.y);
+      ogl[e * npair + k] = p;
+    }
+  }
+}
+
+}  // namespace
+
+// ---- launchers -----------------------------------------------------------------------------------
+
+static int blocks_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
+
+cudaError_t launch_assemble(const LevelCluster* lc, int nl, int64_t total, const ClusterGlobal* cg,
+                            const int32_t* maps, c64* F, c64* S, c64* L, c64* LS, int64_t aug_es,
+                            int64_t sq_es, int ne, int do_lesser, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  int b = std::min(blocks_for(total, 256), 152 * 16);
+  k_assemble<<<b, 256, 0, s>>>(lc, nl, total, cg, maps, F, S, L, LS, aug_es, sq_es, ne, do_lesser);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_a(const LevelCluster* lc, int nl, int64_t max_h, int max_n, const int32_t* h_rq,
+                         const int64_t* h_vi, const c64* hval, const int32_t* own_contact,
+                         const double* E, double eta, const c64* sr, const c64* sl, int64_t ncs,
+                         c64* F, c64* L, int64_t aug_es, int ne, cudaStream_t s) {
+  if (max_h > 0) {
+    dim3 g(blocks_for(max_h, 256), nl);
+    k_add_h<<<g, 256, 0, s>>>(lc, h_rq, h_vi, hval, F, aug_es, ne);
+  }
+  dim3 g2(blocks_for(max_n, 256), nl);
+  k_add_diag<<<g2, 256, 0, s>>>(lc, own_contact, E, eta, sr, sl, ncs, F, L, aug_es, ne);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es, int32_t* piv,
+                            int64_t piv_es, c64* Mt, c64* Rt, int64_t t_es, int k0, int nb, int ne,
+                            int* flag, cudaStream_t s) {
+  k_gj_panel<<<dim3(nmat, ne), GJ_THREADS, 0, s>>>(probs, F, f_es, piv, piv_es, Mt, Rt, t_es, k0, nb, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
+                           const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
+                           int ne, cudaStream_t s) {
+  k_gj_swap<<<dim3(blocks_for(max_n, 128), nmat, ne), 128, 0, s>>>(probs, F, f_es, piv, piv_es, Rt,
+                                                                   t_es, k0, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
+                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s) {
+  size_t sm = (size_t)max_n * (sizeof(c64) + sizeof(int));
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_gj_colperm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gj_colperm<<<dim3(nmat, ne), 256, sm, s>>>(probs, F, f_es, piv, piv_es);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const LevelCluster* lc, int nl, int64_t max_sq, c64* LS, int64_t sq_es,
+                        const c64* Z, int64_t tz_es, int ne, cudaStream_t s) {
+  if (max_sq <= 0) return cudaSuccess;
+  k_fold<<<dim3(blocks_for(max_sq, 256), nl), 256, 0, s>>>(lc, LS, sq_es, Z, tz_es, ne);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const LevelCluster* lc, int nl, int64_t max_sq, const ClusterGlobal* cg,
+                          const int32_t* u_owner, const int32_t* u_local, const int32_t* u_seg,
+                          const int32_t* posmap, const c64* G, const c64* P, int64_t aug_es,
+                          c64* GUU, c64* PUU, int64_t tz_es, int ne, int* flag, cudaStream_t s) {
+  if (max_sq <= 0) return cudaSuccess;
+  k_gather<<<dim3(blocks_for(max_sq, 256), nl), 256, 0, s>>>(lc, cg, u_owner, u_local, u_seg, posmap,
+                                                             G, P, aug_es, GUU, PUU, tz_es, ne, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out(const int64_t* doff, int64_t n, const int64_t* poff, int64_t npair,
+                       const c64* G, const c64* P, int64_t aug_es, c64* ogr, c64* ogl, c64* pgr,
+                       c64* pgl, int ne, cudaStream_t s) {
+  k_out_diag<<<blocks_for(n, 256), 256, 0, s>>>(doff, n, G, P, aug_es, ogr, ogl, ne);
+  if (npair > 0)
+    k_out_pairs<<<blocks_for(npair, 256), 256, 0, s>>>(poff, npair, G, P, aug_es, pgr, pgl, ne);
+  return cudaGetLastError();
+}
+
+}  // namespace hsc

@@ -1,0 +1,809 @@
+// Device driver of hsc_solve: uploads the analysis, builds the per-level launch schedules and runs
+// Algorithm 1 (upward Schur fold, root inverse, downward selected inverse) and Algorithm 2 (the
+// lesser fold and its downward pass) for waves of energies, complex128 throughout.
+//
+// Per cluster i (n own unknowns, m update-set unknowns U_i), per energy:
+//   front     [A_ii | A_iU] = original entries + children's Schur updates (extend-add)
+//   D_i^{-1}  Gauss-Jordan with partial pivoting inside the block, in place of A_ii (Eq. 3)
+//   X_i       = D_i^{-1} A_iU  (= -Psi_iU of Algorithm 1)
+//   S_i      += -A_iU^T X_i    (the Schur update A_jk + Psi_ij^T A_ik of Algorithm 1)
+//   lesser    T = (1/2) L_ii conj(X) - L_iU,  Z = X^T T,  LS_i += Z - Z^dagger   (Algorithm 2's fold
+//             with the (G^r)^dagger factor of N = Sigma^< (G^r)^dagger applied in the downward pass)
+//   downward  G_iU = -X G_UU;  G_ii = D^{-1} - X G_iU^T                        (Algorithm 1)
+//             W = D^{-1} [L_ii conj(G_ii) + L_iU conj(G_Ui) | L_ii conj(G_iU) + L_iU conj(G_UU)]
+//             P_iU = W_iU - X P_UU;  P_ii = W_ii + X P_iU^dagger              (Algorithm 2)
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "kernels.cuh"
+
+namespace hsc {
+
+struct UpLevel {
+  int nl = 0;
+  int64_t lc = 0;           // index into the LevelCluster array
+  int64_t total = 0, max_h = 0, max_sq = 0;
+  double asm_bytes = 0, gather_bytes = 0;   // algorithmic bytes per energy
+  int max_n = 0;
+  bool any_lesser = false;
+  GemmArgs u1{}, u2{}, u3{}, u4{};
+  int64_t gj = 0;           // index into the GJProb array
+  int nmat = 0;
+  std::vector<GemmArgs> steps;
+};
+
+struct DownLevel {
+  int nl = 0;
+  int64_t lc = 0;
+  int64_t max_sq = 0;
+  bool any_lesser = false;
+  double gather_bytes = 0;
+  GemmArgs d[9]{};
+};
+
+enum KClass { K_GEMM = 0, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
+              K_OUT, K_NCLASS };
+static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gj_panel", "gj_swap", "gj_colperm",
+                                           "assemble", "add_a", "lesser_fold", "gather", "out"};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // pairs (start, stop)
+  size_t used = 0;                 // pairs in use
+  std::vector<int> cls;
+  std::vector<double> flops, bytes;
+  int64_t launches[K_NCLASS] = {0};
+};
+
+struct DeviceState {
+  int device = -1;
+  Prof prof;
+  bool planned = false;
+  int nb = 16;                       // Gauss-Jordan panel width
+  // energy-independent device arrays
+  ClusterGlobal* cg = nullptr;
+  LevelCluster* lcs = nullptr;
+  GJProb* gjp = nullptr;
+  GemmProb* gp = nullptr;
+  int32_t *maps = nullptr, *h_rq = nullptr, *own_contact = nullptr;
+  int64_t *h_vi = nullptr, *doff = nullptr;
+  c64* hval = nullptr;
+  int32_t *u_owner = nullptr, *u_local = nullptr, *u_seg = nullptr, *posmap = nullptr;
+  int* flag = nullptr;
+  std::vector<UpLevel> up;
+  std::vector<DownLevel> down;
+  // per-energy strides (elements)
+  int64_t aug_es = 0, sq_es = 0, x_es = 0, tt_es = 0, tz_es = 0, tn_es = 0, gjt_es = 0, piv_es = 0;
+  // workspace for `cap` energies
+  int64_t cap = 0;
+  void* arena = nullptr;
+  c64 *F = nullptr, *L = nullptr, *G = nullptr, *P = nullptr, *S = nullptr, *LS = nullptr,
+      *X = nullptr, *T = nullptr, *Z = nullptr, *GUU = nullptr, *PUU = nullptr, *N = nullptr,
+      *GJT = nullptr;
+  int32_t* piv = nullptr;
+  // host-io staging
+  int64_t io_cap = 0, io_n = 0, io_ncs = 0, io_req = 0;
+  void* io = nullptr;
+  std::vector<void*> fixed;          // energy-independent allocations
+};
+
+void device_state_free(DeviceState* d) {
+  if (!d) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (d->device >= 0) cudaSetDevice(d->device);
+  for (void* p : d->fixed) cudaFree(p);
+  for (cudaEvent_t e : d->prof.pool) cudaEventDestroy(e);
+  if (d->arena) cudaFree(d->arena);
+  if (d->io) cudaFree(d->io);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete d;
+}
+
+namespace {
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess)                                                        \
+      return hsc_fail(h, HSC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(DeviceState* d, T** dst, const std::vector<T>& v) {
+  *dst = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  d->fixed.push_back(*dst);
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+constexpr int TILE = 64;
+
+struct GemmList {
+  std::vector<GemmProb>& all;
+  size_t start;
+  int tiles = 0;
+  int count = 0;
+  double flops = 0;
+  explicit GemmList(std::vector<GemmProb>& a) : all(a), start(a.size()) {}
+  void add(int M, int N, int K, int64_t a, int lda, int64_t b, int ldb, int64_t c, int ldc,
+           int64_t dd = 0, int ldd = 0, int use_d = 0, int zr0 = 0, int zr1 = 0) {
+    if (M <= 0 || N <= 0) return;
+    if (all.size() != start + (size_t)count) throw std::logic_error("interleaved GEMM lists");
+    ++count;
+    GemmProb p{};
+    p.M = M; p.N = N; p.K = K;
+    p.a = a; p.lda = lda; p.b = b; p.ldb = ldb; p.c = c; p.ldc = ldc; p.d = dd; p.ldd = ldd;
+    p.use_d = use_d; p.zr0 = zr0; p.zr1 = zr1;
+    p.tiles_n = (N + TILE - 1) / TILE;
+    p.tile_start = tiles;
+    flops += 8.0 * M * N * K;
+    tiles += ((M + TILE - 1) / TILE) * p.tiles_n;
+    all.push_back(p);
+  }
+  // records the list in a GemmArgs; the device pointer is patched after upload
+  GemmArgs args(int opa, int opb, double ar, double ai, double br, double bi) const {
+    GemmArgs g{};
+    g.probs = reinterpret_cast<const GemmProb*>(start);   // index, patched later
+    g.nprob = (int)(all.size() - start);
+    g.total_tiles = tiles;
+    g.opa = opa; g.opb = opb;
+    g.ar = ar; g.ai = ai; g.br = br; g.bi = bi;
+    g.flops = flops;
+    return g;
+  }
+};
+
+int build_schedule(hsc_ctx* h) {
+  DeviceState* d = h->dev;
+  const Plan& P = h->plan;
+  const int nc = (int)P.cl.size();
+  const int nb = d->nb;
+  std::vector<ClusterGlobal> cg(nc);
+  std::vector<int64_t> xoff(nc);
+  int64_t xs = 0;
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = P.cl[i];
+    cg[i] = ClusterGlobal{(int)c.n, (int)c.m, c.depth, c.lesser ? 1 : 0, P.off[i].aug, P.off[i].sq};
+    xoff[i] = xs;
+    xs += c.n * c.m;
+  }
+  d->aug_es = P.tot_aug;
+  d->sq_es = P.tot_sq;
+  d->x_es = std::max<int64_t>(xs, 1);
+  d->piv_es = std::max<int64_t>(P.n, 1);
+
+  std::vector<LevelCluster> lcs;
+  std::vector<GJProb> gjs;
+  std::vector<GemmProb> gps;
+  int64_t tt_max = 1, tz_max = 1, tn_max = 1, gjt_max = 1;
+
+  auto base_lc = [&](int i) {
+    const Cluster& c = P.cl[i];
+    LevelCluster L{};
+    L.n = (int)c.n; L.m = (int)c.m; L.lesser = c.lesser ? 1 : 0;
+    L.child[0] = c.child[0]; L.child[1] = c.child[1];
+    L.aug = P.off[i].aug; L.sq = P.off[i].sq; L.x = xoff[i];
+    L.map0 = P.map_off[2 * i] < 0 ? 0 : P.map_off[2 * i];
+    L.map1 = P.map_off[2 * i + 1] < 0 ? 0 : P.map_off[2 * i + 1];
+    L.h0 = P.h_off[i]; L.h1 = P.h_off[i + 1];
+    L.own0 = P.own_off[i];
+    L.u0 = P.u_off[i]; L.pm0 = P.pm_off[i]; L.nseg = P.nseg[i]; L.depth = c.depth;
+    return L;
+  };
+
+  // upward levels
+  d->up.assign(P.by_height.size(), UpLevel());
+  for (size_t hl = 0; hl < P.by_height.size(); ++hl) {
+    UpLevel& U = d->up[hl];
+    const auto& ids = P.by_height[hl];
+    U.lc = (int64_t)lcs.size();
+    U.nl = (int)ids.size();
+    int64_t el = 0, tt = 0, tz = 0, gjt = 0;
+    for (int i : ids) {
+      LevelCluster L = base_lc(i);
+      L.elem_start = el;
+      L.tt = tt; L.tz = tz; L.tn = 0;
+      el += (int64_t)L.n * (L.n + L.m) + (int64_t)L.m * L.m;
+      tt += (int64_t)L.n * L.m;
+      tz += (int64_t)L.m * L.m;
+      U.max_h = std::max(U.max_h, L.h1 - L.h0);
+      U.max_n = std::max(U.max_n, L.n);
+      U.max_sq = std::max(U.max_sq, (int64_t)L.m * L.m);
+      U.any_lesser |= L.lesser != 0;
+      {
+        double b = 16.0 * ((double)L.n * (L.n + L.m) + (double)L.m * L.m);
+        for (int k = 0; k < 2; ++k)
+          if (L.child[k] >= 0) b += 16.0 * (double)P.cl[L.child[k]].m * P.cl[L.child[k]].m;
+        U.asm_bytes += L.lesser ? 2 * b : b;
+      }
+      lcs.push_back(L);
+      GJProb g{};
+      g.n = L.n; g.ld = L.n + L.m; g.off = L.aug; g.piv_off = L.own0;
+      g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * nb;
+      gjt += 2 * (int64_t)L.n * nb;
+      gjs.push_back(g);
+    }
+    U.total = el;
+    tt_max = std::max(tt_max, tt);
+    tz_max = std::max(tz_max, tz);
+    gjt_max = std::max(gjt_max, gjt);
+    U.gj = (int64_t)gjs.size() - U.nl;
+    U.nmat = U.nl;
+    const LevelCluster* lv = lcs.data() + U.lc;
+    {
+      GemmList g1(gps);
+      for (int k = 0; k < U.nl; ++k) {
+        const auto& L = lv[k];
+        g1.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.x, L.m);
+      }
+      U.u1 = g1.args(OP_N, OP_N, 1, 0, 0, 0);
+      GemmList g2(gps);
+      for (int k = 0; k < U.nl; ++k) {
+        const auto& L = lv[k];
+        g2.add(L.m, L.m, L.n, L.aug + L.n, L.n + L.m, L.x, L.m, L.sq, L.m, L.sq, L.m, 1);
+      }
+      U.u2 = g2.args(OP_T, OP_N, -1, 0, 1, 0);
+      GemmList g3(gps);
+      for (int k = 0; k < U.nl; ++k) {
+        const auto& L = lv[k];
+        if (L.lesser)
+          g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.x, L.m, L.tt, L.m, L.aug + L.n, L.n + L.m, 1);
+      }
+      U.u3 = g3.args(OP_N, OP_C, 0.5, 0, -1, 0);
+      GemmList g4(gps);
+      for (int k = 0; k < U.nl; ++k) {
+        const auto& L = lv[k];
+        if (L.lesser) g4.add(L.m, L.m, L.n, L.x, L.m, L.tt, L.m, L.tz, L.m);
+      }
+      U.u4 = g4.args(OP_T, OP_N, 1, 0, 0, 0);
+      const GJProb* gl = gjs.data() + U.gj;
+      for (int k0 = 0; k0 < U.max_n; k0 += nb) {
+        GemmList gs(gps);
+        for (int k = 0; k < U.nl; ++k) {
+          const GJProb& q = gl[k];
+          if (q.n <= k0) continue;
+          int w = std::min(nb, q.n - k0);
+          gs.add(q.n, q.n, w, q.mt_off, nb, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k0, k0 + w);
+        }
+        U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+      }
+    }
+  }
+
+  // downward levels
+  d->down.assign(P.by_depth.size(), DownLevel());
+  for (size_t dl = 0; dl < P.by_depth.size(); ++dl) {
+    DownLevel& D = d->down[dl];
+    const auto& ids = P.by_depth[dl];
+    D.lc = (int64_t)lcs.size();
+    D.nl = (int)ids.size();
+    int64_t tz = 0, tn = 0;
+    for (int i : ids) {
+      LevelCluster L = base_lc(i);
+      L.tz = tz; L.tn = tn; L.tt = 0; L.elem_start = 0;
+      tz += (int64_t)L.m * L.m;
+      tn += (int64_t)L.n * (L.n + L.m);
+      D.max_sq = std::max(D.max_sq, (int64_t)L.m * L.m);
+      D.any_lesser |= L.lesser != 0;
+      D.gather_bytes += 2 * 32.0 * (double)L.m * L.m;
+      lcs.push_back(L);
+    }
+    tz_max = std::max(tz_max, tz);
+    tn_max = std::max(tn_max, tn);
+    const LevelCluster* lv = lcs.data() + D.lc;
+    GemmList g1(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      g1.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m);
+    }
+    D.d[0] = g1.args(OP_N, OP_N, -1, 0, 0, 0);
+    GemmList g2(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      g2.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, 1);
+    }
+    D.d[1] = g2.args(OP_N, OP_T, -1, 0, 1, 0);
+    GemmList g3(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      if (L.lesser) g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn + L.n, L.n + L.m);
+    }
+    D.d[2] = g3.args(OP_N, OP_C, 1, 0, 0, 0);
+    GemmList g4(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      if (L.lesser)
+        g4.add(L.n, L.m, L.m, L.aug + L.n, L.n + L.m, L.tz, L.m, L.tn + L.n, L.n + L.m, L.tn + L.n, L.n + L.m, 1);
+    }
+    D.d[3] = g4.args(OP_N, OP_C, 1, 0, 1, 0);
+    GemmList g5(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      if (L.lesser) g5.add(L.n, L.n, L.n, L.aug, L.n + L.m, L.aug, L.n + L.m, L.tn, L.n + L.m);
+    }
+    D.d[4] = g5.args(OP_N, OP_C, 1, 0, 0, 0);
+    GemmList g6(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      if (L.lesser)
+        g6.add(L.n, L.n, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn, L.n + L.m, L.tn, L.n + L.m, 1);
+    }
+    D.d[5] = g6.args(OP_N, OP_H, 1, 0, 1, 0);
+    GemmList g7(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      if (L.lesser) g7.add(L.n, L.n + L.m, L.n, L.aug, L.n + L.m, L.tn, L.n + L.m, L.aug, L.n + L.m);
+    }
+    D.d[6] = g7.args(OP_N, OP_N, 1, 0, 0, 0);
+    GemmList g8(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      g8.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.lesser);
+    }
+    D.d[7] = g8.args(OP_N, OP_N, -1, 0, 1, 0);
+    GemmList g9(gps);
+    for (int k = 0; k < D.nl; ++k) {
+      const auto& L = lv[k];
+      g9.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, L.lesser);
+    }
+    D.d[8] = g9.args(OP_N, OP_H, 1, 0, 1, 0);
+  }
+  d->tt_es = tt_max;
+  d->tz_es = tz_max;
+  d->tn_es = tn_max;
+  d->gjt_es = gjt_max;
+
+  // diag output offsets
+  std::vector<int64_t> doff(P.n);
+  for (int64_t u = 0; u < P.n; ++u) {
+    int c = P.unk_cluster[u];
+    int64_t l = P.unk_local[u];
+    doff[u] = P.off[c].aug + l * (P.cl[c].n + P.cl[c].m) + l;
+  }
+  std::vector<c64> hv(h->val.size());
+  for (size_t k = 0; k < hv.size(); ++k) hv[k] = make_double2(h->val[k].re, h->val[k].im);
+
+  cudaError_t e = cudaSuccess;
+#define UP(dst, v) if ((e = upload(d, dst, v)) != cudaSuccess) return hsc_fail(h, HSC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e))
+  UP(&d->cg, cg);
+  UP(&d->lcs, lcs);
+  UP(&d->gjp, gjs);
+  UP(&d->gp, gps);
+  UP(&d->maps, P.map_child);
+  UP(&d->h_rq, P.h_rq);
+  UP(&d->h_vi, P.h_vi);
+  UP(&d->hval, hv);
+  UP(&d->own_contact, P.own_contact);
+  UP(&d->u_owner, P.u_owner);
+  UP(&d->u_local, P.u_local);
+  UP(&d->u_seg, P.u_seg);
+  UP(&d->posmap, P.posmap);
+  UP(&d->doff, doff);
+#undef UP
+  if ((e = cudaMalloc((void**)&d->flag, 4 * sizeof(int))) != cudaSuccess)
+    return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc flag");
+  d->fixed.push_back(d->flag);
+  // patch problem-list pointers
+  auto patch = [&](GemmArgs& g) { g.probs = d->gp + reinterpret_cast<size_t>(g.probs); };
+  for (auto& U : d->up) {
+    patch(U.u1); patch(U.u2); patch(U.u3); patch(U.u4);
+    for (auto& s : U.steps) patch(s);
+  }
+  for (auto& D : d->down)
+    for (auto& g : D.d) patch(g);
+  d->planned = true;
+  return HSC_OK;
+}
+
+int64_t bytes_per_energy(const DeviceState* d) {
+  int64_t c = 4 * d->aug_es + 2 * d->sq_es + d->x_es + d->tt_es + 3 * d->tz_es + d->tn_es + d->gjt_es;
+  return c * (int64_t)sizeof(c64) + d->piv_es * 4;
+}
+
+int ensure_arena(hsc_ctx* h, int64_t want) {
+  DeviceState* d = h->dev;
+  if (d->cap >= want) return HSC_OK;
+  if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->cap = 0; }
+  size_t bytes = (size_t)bytes_per_energy(d) * want + 64 * 256;
+  cudaError_t e = cudaMalloc(&d->arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc workspace (" + std::to_string(bytes >> 20) + " MiB)");
+  }
+  char* p = (char*)d->arena;
+  auto take = [&](int64_t elems, size_t esz) {
+    char* r = p;
+    p += ((size_t)elems * want * esz + 255) / 256 * 256;
+    return r;
+  };
+  d->F = (c64*)take(d->aug_es, 16);
+  d->L = (c64*)take(d->aug_es, 16);
+  d->G = (c64*)take(d->aug_es, 16);
+  d->P = (c64*)take(d->aug_es, 16);
+  d->S = (c64*)take(d->sq_es, 16);
+  d->LS = (c64*)take(d->sq_es, 16);
+  d->X = (c64*)take(d->x_es, 16);
+  d->T = (c64*)take(d->tt_es, 16);
+  d->Z = (c64*)take(d->tz_es, 16);
+  d->GUU = (c64*)take(d->tz_es, 16);
+  d->PUU = (c64*)take(d->tz_es, 16);
+  d->N = (c64*)take(d->tn_es, 16);
+  d->GJT = (c64*)take(d->gjt_es, 16);
+  d->piv = (int32_t*)take(d->piv_es, 4);
+  d->cap = want;
+  return HSC_OK;
+}
+
+GemmArgs bind(GemmArgs g, const c64* A, int64_t aes, const c64* B, int64_t bes, c64* C, int64_t ces,
+              const c64* D, int64_t des) {
+  g.A = A; g.a_es = aes; g.B = B; g.b_es = bes; g.C = C; g.c_es = ces; g.D = D; g.d_es = des;
+  return g;
+}
+
+cudaError_t prof_start(DeviceState* d, cudaStream_t s) {
+  Prof& p = d->prof;
+  if (!p.on) return cudaSuccess;
+  if (2 * (p.used + 1) > p.pool.size()) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      p.pool.push_back(e);
+    }
+  }
+  return cudaEventRecord(p.pool[2 * p.used], s);
+}
+
+cudaError_t prof_stop(DeviceState* d, cudaStream_t s, int cls, int nk, double flops, double bytes) {
+  Prof& p = d->prof;
+  p.launches[cls] += nk;
+  if (!p.on) return cudaSuccess;
+  cudaError_t err = cudaEventRecord(p.pool[2 * p.used + 1], s);
+  p.cls.push_back(cls);
+  p.flops.push_back(flops);
+  p.bytes.push_back(bytes);
+  ++p.used;
+  return err;
+}
+
+#define LAUNCH(cls, nk, fl, by, call)                 \
+  do {                                                \
+    CK(prof_start(d, s));                             \
+    CK(call);                                         \
+    CK(prof_stop(d, s, cls, nk, fl, by));             \
+  } while (0)
+
+// One wave of `ne` energies with inputs already on the device.
+int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, const c64* sl,
+             int64_t npair, const int64_t* poff, c64* ogr, c64* ogl, c64* pgr, c64* pgl,
+             cudaStream_t s) {
+  DeviceState* d = h->dev;
+  const bool les = sl != nullptr;
+  const int64_t ncs = h->n_contact_unknowns;
+  // ---- upward (Algorithm 1 first loop, Algorithm 2 fold) ----
+  auto gemm = [&](const GemmArgs& g) -> int {
+    if (g.total_tiles <= 0) return HSC_OK;
+    LAUNCH(K_GEMM, 1, g.flops * ne, 0.0, gemm_z(g, ne, s));
+    return HSC_OK;
+  };
+#define GEMM(g) do { int _r = gemm(g); if (_r != HSC_OK) return _r; } while (0)
+  for (auto& U : d->up) {
+    const LevelCluster* lc = d->lcs + U.lc;
+    LAUNCH(K_ASSEMBLE, 1, 0.0, U.asm_bytes * ne,
+           launch_assemble(lc, U.nl, U.total, d->cg, d->maps, d->F, d->S, d->L, d->LS, d->aug_es,
+                           d->sq_es, ne, les ? 1 : 0, s));
+    LAUNCH(K_ADD_A, 2, 0.0, 0.0,
+           launch_add_a(lc, U.nl, U.max_h, U.max_n, d->h_rq, d->h_vi, d->hval, d->own_contact, E,
+                        eta, sr, sl, ncs, d->F, d->L, d->aug_es, ne, s));
+    // Gauss-Jordan inversion of A_ii in place (D_i^{-1}), panel by panel
+    const GJProb* gp = d->gjp + U.gj;
+    for (size_t st = 0; st < U.steps.size(); ++st) {
+      const int k0 = (int)st * d->nb;
+      LAUNCH(K_GJ_PANEL, 1, 0.0, 0.0,
+             launch_gj_panel(gp, U.nmat, d->F, d->aug_es, d->piv, d->piv_es, d->GJT, d->GJT,
+                             d->gjt_es, k0, d->nb, ne, d->flag, s));
+      LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
+             launch_gj_swap(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
+                            d->gjt_es, k0, d->nb, ne, s));
+      GEMM(bind(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es));
+    }
+    LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
+           launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s));
+    GEMM(bind(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0));
+    GEMM(bind(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es));
+    if (les && U.any_lesser) {
+      GEMM(bind(U.u3, d->L, d->aug_es, d->X, d->x_es, d->T, d->tt_es, d->L, d->aug_es));
+      GEMM(bind(U.u4, d->X, d->x_es, d->T, d->tt_es, d->Z, d->tz_es, nullptr, 0));
+      LAUNCH(K_FOLD, 1, 0.0, 0.0, launch_fold(lc, U.nl, U.max_sq, d->LS, d->sq_es, d->Z, d->tz_es, ne, s));
+    }
+  }
+  // ---- downward (Algorithm 1 second loop, Algorithm 2 second loop) ----
+  for (auto& D : d->down) {
+    const LevelCluster* lc = d->lcs + D.lc;
+    if (D.max_sq > 0)
+      LAUNCH(K_GATHER, 1, 0.0, D.gather_bytes * ne * (les ? 1.0 : 0.5),
+             launch_gather(lc, D.nl, D.max_sq, d->cg, d->u_owner, d->u_local, d->u_seg, d->posmap,
+                           d->G, d->P, d->aug_es, d->GUU, les ? d->PUU : nullptr, d->tz_es, ne,
+                           d->flag + 1, s));
+    GEMM(bind(D.d[0], d->X, d->x_es, d->GUU, d->tz_es, d->G, d->aug_es, nullptr, 0));
+    GEMM(bind(D.d[1], d->X, d->x_es, d->G, d->aug_es, d->G, d->aug_es, d->F, d->aug_es));
+    if (!les) continue;
+    if (D.any_lesser) {
+      GEMM(bind(D.d[2], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0));
+      GEMM(bind(D.d[3], d->L, d->aug_es, d->GUU, d->tz_es, d->N, d->tn_es, d->N, d->tn_es));
+      GEMM(bind(D.d[4], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0));
+      GEMM(bind(D.d[5], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, d->N, d->tn_es));
+      GEMM(bind(D.d[6], d->F, d->aug_es, d->N, d->tn_es, d->P, d->aug_es, nullptr, 0));
+    }
+    GEMM(bind(D.d[7], d->X, d->x_es, d->PUU, d->tz_es, d->P, d->aug_es, d->P, d->aug_es));
+    GEMM(bind(D.d[8], d->X, d->x_es, d->P, d->aug_es, d->P, d->aug_es, d->P, d->aug_es));
+  }
+#undef GEMM
+  LAUNCH(K_OUT, npair > 0 ? 2 : 1, 0.0, 32.0 * (double)(h->n + npair) * ne * (les ? 2 : 1),
+         launch_out(d->doff, h->n, poff, npair, d->G, d->P, d->aug_es, ogr, les ? ogl : nullptr, pgr,
+                    les ? pgl : nullptr, ne, s));
+  return HSC_OK;
+}
+
+// locate a requested pair in the stored G blocks; negative = transposed source (-off-1)
+int locate_pair(const Plan& P, int64_t a, int64_t b, int64_t* out) {
+  int ca = P.unk_cluster[a], cb = P.unk_cluster[b];
+  int64_t la = P.unk_local[a], lb = P.unk_local[b];
+  auto anc = [&](int x, int i) { return P.cl[x].first_desc <= i && i < x; };
+  auto upos = [&](int i, int64_t u) -> int64_t {
+    // position of unknown u in U_i (unknown granularity)
+    int64_t base = P.u_off[i], m = P.cl[i].m;
+    int c = P.unk_cluster[u];
+    int64_t l = P.unk_local[u];
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      int oc = P.u_owner[base + mid];
+      int64_t ol = P.u_local[base + mid];
+      if (oc < c || (oc == c && ol < l)) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < m && P.u_owner[base + lo] == c && P.u_local[base + lo] == l) return lo;
+    return -1;
+  };
+  if (ca == cb) { *out = P.off[ca].aug + la * (P.cl[ca].n + P.cl[ca].m) + lb; return 1; }
+  if (anc(cb, ca)) {
+    int64_t k = upos(ca, b);
+    if (k < 0) return 0;
+    *out = P.off[ca].aug + la * (P.cl[ca].n + P.cl[ca].m) + P.cl[ca].n + k;
+    return 1;
+  }
+  if (anc(ca, cb)) {
+    int64_t k = upos(cb, a);
+    if (k < 0) return 0;
+    *out = -(P.off[cb].aug + lb * (P.cl[cb].n + P.cl[cb].m) + P.cl[cb].n + k) - 1;
+    return 1;
+  }
+  return 0;
+}
+
+int64_t budget_bytes() {
+  const char* env = getenv("HSC_WORKSPACE_GB");
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  int64_t avail = (int64_t)(fr * 0.85) - ((int64_t)2 << 30);
+  if (env) {
+    int64_t want = (int64_t)(atof(env) * (double)(1 << 30));
+    return std::min(want, avail);
+  }
+  return avail;
+}
+
+}  // namespace
+}  // namespace hsc
+
+using namespace hsc;
+
+extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                         const hsc_c128* sigma_less, int32_t precision, int32_t n_req,
+                         const int32_t* req_pairs, hsc_c128* diag_gr, hsc_c128* diag_gl,
+                         hsc_c128* req_gr, hsc_c128* req_gl, void* cuda_stream, int32_t io_on_device) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  if (n_E < 0 || (!E && n_E > 0)) return hsc_fail(h, HSC_ERR_ARG, "bad energy array");
+  if (n_E == 0) return HSC_OK;
+  if (!diag_gr) return hsc_fail(h, HSC_ERR_ARG, "diag_gr is NULL");
+  if (sigma_less && !diag_gl) return hsc_fail(h, HSC_ERR_ARG, "diag_gl is NULL");
+  if (h->n_contact_unknowns > 0 && !sigma_r) return hsc_fail(h, HSC_ERR_ARG, "sigma_r is NULL");
+  if (n_req < 0 || (n_req > 0 && (!req_pairs || !req_gr || (sigma_less && !req_gl))))
+    return hsc_fail(h, HSC_ERR_ARG, "bad requested-pair arrays");
+  if (precision != HSC_FP64) return hsc_fail(h, HSC_ERR_ARG, "precision must be HSC_FP64");
+  if (!(eta >= 0.0)) return hsc_fail(h, HSC_ERR_ARG, "eta must be >= 0");
+  const Plan& P = h->plan;
+  std::vector<int64_t> poff(n_req);
+  for (int k = 0; k < n_req; ++k) {
+    int64_t a = req_pairs[2 * k], b = req_pairs[2 * k + 1];
+    if (a < 0 || a >= h->n || b < 0 || b >= h->n) return hsc_fail(h, HSC_ERR_ARG, "pair index out of range");
+    if (!locate_pair(P, a, b, &poff[k]))
+      return hsc_fail(h, HSC_ERR_NOT_SELECTED, "pair (" + std::to_string(a) + "," + std::to_string(b) +
+                                                   ") is outside the filled pattern");
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (!h->dev) {
+    h->dev = new DeviceState();
+    CK(cudaGetDevice(&h->dev->device));
+  }
+  DeviceState* d = h->dev;
+  int cur = 0;
+  CK(cudaGetDevice(&cur));
+  if (cur != d->device) return hsc_fail(h, HSC_ERR_ARG, "current device differs from the handle's device");
+  if (!d->planned) {
+    int rc;
+    try {
+      rc = build_schedule(h);
+    } catch (const std::exception& ex) {
+      return hsc_fail(h, HSC_ERR_ARG, std::string("schedule: ") + ex.what());
+    }
+    if (rc != HSC_OK) return rc;
+  }
+  const int64_t per = bytes_per_energy(d);
+  int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(budget_bytes() / per, 0));
+  if (d->cap > 0) wave = std::max<int64_t>(std::min<int64_t>(n_E, d->cap), wave);
+  if (wave <= 0) return hsc_fail(h, HSC_ERR_OOM, "one energy needs " + std::to_string(per >> 20) + " MiB of workspace");
+  wave = std::min<int64_t>(wave, 65535);
+  int rc = ensure_arena(h, wave);
+  if (rc != HSC_OK) return rc;
+
+  const int64_t n = h->n, ncs = h->n_contact_unknowns;
+  int64_t* d_poff = nullptr;
+  if (n_req > 0) {
+    CK(cudaMallocAsync((void**)&d_poff, n_req * sizeof(int64_t), s));
+    CK(cudaMemcpyAsync(d_poff, poff.data(), n_req * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(d->flag, 0, 4 * sizeof(int), s));
+  // host io: staging buffers for one wave
+  double* sE = nullptr;
+  c64 *ssr = nullptr, *ssl = nullptr, *sgr = nullptr, *sgl = nullptr, *spr = nullptr, *spl = nullptr;
+  if (!io_on_device) {
+    int64_t need = wave * (int64_t)(8 + 16 * (2 * ncs + 2 * n + 2 * (int64_t)n_req)) + 8 * 256;
+    if (d->io_cap < need) {
+      if (d->io) cudaFree(d->io);
+      d->io = nullptr;
+      d->io_cap = 0;
+      cudaError_t e = cudaMalloc(&d->io, need);
+      if (e != cudaSuccess) { cudaGetLastError(); return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc io staging"); }
+      d->io_cap = need;
+    }
+    char* p = (char*)d->io;
+    auto take = [&](int64_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
+    sE = (double*)take(wave * 8);
+    ssr = (c64*)take(wave * ncs * 16);
+    ssl = (c64*)take(wave * ncs * 16);
+    sgr = (c64*)take(wave * n * 16);
+    sgl = (c64*)take(wave * n * 16);
+    spr = (c64*)take(wave * (int64_t)n_req * 16);
+    spl = (c64*)take(wave * (int64_t)n_req * 16);
+  }
+  for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
+    const int ne = (int)std::min<int64_t>(wave, n_E - e0);
+    const double* dE;
+    const c64 *dsr, *dsl;
+    c64 *ogr, *ogl, *pgr, *pgl;
+    if (io_on_device) {
+      dE = E + e0;
+      dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
+      dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
+      ogr = reinterpret_cast<c64*>(diag_gr) + e0 * n;
+      ogl = diag_gl ? reinterpret_cast<c64*>(diag_gl) + e0 * n : nullptr;
+      pgr = req_gr ? reinterpret_cast<c64*>(req_gr) + e0 * n_req : nullptr;
+      pgl = req_gl ? reinterpret_cast<c64*>(req_gl) + e0 * n_req : nullptr;
+    } else {
+      CK(cudaMemcpyAsync(sE, E + e0, ne * 8, cudaMemcpyHostToDevice, s));
+      if (ncs > 0) {
+        CK(cudaMemcpyAsync(ssr, sigma_r + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
+        if (sigma_less) CK(cudaMemcpyAsync(ssl, sigma_less + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
+      }
+      dE = sE; dsr = ssr; dsl = sigma_less ? ssl : nullptr;
+      ogr = sgr; ogl = sgl; pgr = spr; pgl = spl;
+    }
+    rc = run_wave(h, ne, dE, eta, dsr, dsl, n_req, d_poff, ogr, ogl, pgr, pgl, s);
+    if (rc != HSC_OK) return rc;
+    if (!io_on_device) {
+      CK(cudaMemcpyAsync(diag_gr + e0 * n, sgr, ne * n * 16, cudaMemcpyDeviceToHost, s));
+      if (sigma_less) CK(cudaMemcpyAsync(diag_gl + e0 * n, sgl, ne * n * 16, cudaMemcpyDeviceToHost, s));
+      if (n_req > 0) {
+        CK(cudaMemcpyAsync(req_gr + e0 * n_req, spr, ne * (int64_t)n_req * 16, cudaMemcpyDeviceToHost, s));
+        if (sigma_less) CK(cudaMemcpyAsync(req_gl + e0 * n_req, spl, ne * (int64_t)n_req * 16, cudaMemcpyDeviceToHost, s));
+      }
+    }
+  }
+  if (d_poff) CK(cudaFreeAsync(d_poff, s));
+  int flags[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(flags, d->flag, sizeof(flags), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags[1]) return hsc_fail(h, HSC_ERR_ARG, "internal gather map error");
+  if (flags[0]) return hsc_fail(h, HSC_ERR_SINGULAR, "zero pivot in a cluster block");
+  h->err.clear();
+  return HSC_OK;
+}
+
+extern "C" int hsc_debug_offset(hsc_t h, int32_t i, int64_t* aug, int64_t* sq, int64_t* x) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  const Plan& P = h->plan;
+  if (i < 0 || i >= (int32_t)P.cl.size()) return hsc_fail(h, HSC_ERR_ARG, "cluster out of range");
+  int64_t xs = 0;
+  for (int k = 0; k < i; ++k) xs += P.cl[k].n * P.cl[k].m;
+  if (aug) *aug = P.off[i].aug;
+  if (sq) *sq = P.off[i].sq;
+  if (x) *x = xs;
+  return HSC_OK;
+}
+
+extern "C" int hsc_debug_blocks(hsc_t h, int32_t which, int32_t energy, hsc_c128* out, int64_t* count) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  DeviceState* d = h->dev;
+  if (!d || !d->arena) return hsc_fail(h, HSC_ERR_STATE, "no solve has run");
+  if (energy < 0 || energy >= d->cap || !count) return hsc_fail(h, HSC_ERR_ARG, "bad energy/count");
+  const c64* base = nullptr;
+  int64_t es = 0;
+  switch (which) {
+    case 0: base = d->F; es = d->aug_es; break;
+    case 1: base = d->L; es = d->aug_es; break;
+    case 2: base = d->G; es = d->aug_es; break;
+    case 3: base = d->P; es = d->aug_es; break;
+    case 4: base = d->S; es = d->sq_es; break;
+    case 5: base = d->LS; es = d->sq_es; break;
+    case 6: base = d->X; es = d->x_es; break;
+    default: return hsc_fail(h, HSC_ERR_ARG, "bad block array id");
+  }
+  *count = es;
+  if (!out) return HSC_OK;
+  CK(cudaMemcpy(out, base + (int64_t)energy * es, es * sizeof(c64), cudaMemcpyDeviceToHost));
+  return HSC_OK;
+}
+
+extern "C" int hsc_profile(hsc_t h, int32_t enable) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!h->dev) {
+    h->dev = new DeviceState();
+    CK(cudaGetDevice(&h->dev->device));
+  }
+  Prof& p = h->dev->prof;
+  p.on = enable != 0;
+  p.used = 0;
+  p.cls.clear();
+  p.flops.clear();
+  p.bytes.clear();
+  for (auto& l : p.launches) l = 0;
+  return HSC_OK;
+}
+
+extern "C" int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int32_t* n_out) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!n_out) return hsc_fail(h, HSC_ERR_ARG, "n_out is NULL");
+  *n_out = K_NCLASS;
+  if (!out) return HSC_OK;
+  if (cap < K_NCLASS) return hsc_fail(h, HSC_ERR_ARG, "cap too small");
+  for (int c = 0; c < K_NCLASS; ++c) {
+    std::memset(&out[c], 0, sizeof(hsc_kernel_stat));
+    std::strncpy(out[c].name, kClassName[c], sizeof(out[c].name) - 1);
+  }
+  DeviceState* d = h->dev;
+  if (!d) return HSC_OK;
+  Prof& p = d->prof;
+  for (size_t k = 0; k < p.used; ++k) {
+    CK(cudaEventSynchronize(p.pool[2 * k + 1]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, p.pool[2 * k], p.pool[2 * k + 1]));
+    out[p.cls[k]].ms += ms;
+    out[p.cls[k]].timed += 1;
+    out[p.cls[k]].flops += p.flops[k];
+    out[p.cls[k]].bytes += p.bytes[k];
+  }
+  for (int c = 0; c < K_NCLASS; ++c) out[c].launches = p.launches[c];
+  return HSC_OK;
+}

@@ -17,8 +17,8 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
           4: "HSC_ERR_SINGULAR", 5: "HSC_ERR_NOT_SELECTED", 6: "HSC_ERR_OOM", 7: "HSC_ERR_CUDA",
           8: "HSC_ERR_TIMEOUT"}
 
-EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_last_error",
-           "hsc_destroy"]
+EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_profile",
+           "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_last_error", "hsc_destroy"]
 
 
 class hsc_tree_stats(ctypes.Structure):
@@ -33,6 +33,11 @@ class hsc_cluster_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("parent", ctypes.c_int32),
                 ("child", ctypes.c_int32 * 2), ("height", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("lesser", ctypes.c_int32)]
+
+
+class hsc_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("timed", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class HSCError(RuntimeError):
@@ -63,10 +68,14 @@ def load():
     L.hsc_analyze.argtypes = [vp, i32, ctypes.POINTER(hsc_tree_stats)]
     L.hsc_cluster.argtypes = [vp, i32, ctypes.POINTER(hsc_cluster_info), vp, vp]
     L.hsc_solve.argtypes = [vp, i64, vp, dp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, i32]
+    L.hsc_profile.argtypes = [vp, i32]
+    L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(hsc_kernel_stat), i32, ctypes.POINTER(i32)]
+    L.hsc_device_fp64_peaks.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
     L.hsc_last_error.argtypes = [vp]
     L.hsc_last_error.restype = ctypes.c_char_p
     L.hsc_destroy.argtypes = [vp]
-    for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_destroy"):
+    for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_profile",
+                 "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -140,6 +149,27 @@ def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, dia
                             int(precision), n_req, _ptr(pairs), _ptr(diag_gr), _ptr(diag_gl),
                             _ptr(req_gr), _ptr(req_gl), s, 1 if io_on_device else 0)
     _check(h, code)
+
+
+def hsc_profile(h, enable):
+    _check(h, load().hsc_profile(h, 1 if enable else 0))
+
+
+def hsc_profile_read(h):
+    """Per-kernel-class statistics as a list of dicts (name, launches, timed, ms, flops, bytes)."""
+    n = ctypes.c_int32()
+    _check(h, load().hsc_profile_read(h, None, 0, ctypes.byref(n)))
+    arr = (hsc_kernel_stat * n.value)()
+    _check(h, load().hsc_profile_read(h, arr, n.value, ctypes.byref(n)))
+    return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, ms=a.ms, flops=a.flops,
+                 bytes=a.bytes) for a in arr]
+
+
+def hsc_device_fp64_peaks():
+    """(FP64 tensor-pipe GFLOP/s, scalar FP64 FMA GFLOP/s) measured on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(None, load().hsc_device_fp64_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def hsc_last_error(h=None):

@@ -1,0 +1,147 @@
+"""CPU tests of the C ABI (library loads, every declared symbol is exported, host-side errors) and
+of the host analysis (nested dissection, update sets, operation-count model). No GPU needed."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1702_05167_gb300 import hsc, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not os.path.exists(hsc.lib_path()):
+        from paper_1702_05167_gb300 import build
+        build.build()
+    hsc.load()
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?[\w\*\s]+?\b(hsc_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_symbols()
+    assert {"hsc_create", "hsc_analyze", "hsc_solve", "hsc_destroy", "hsc_last_error"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", hsc.lib_path()], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (hsc_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = hsc.load()
+    for n in names:
+        assert hasattr(L, n)
+
+
+def _handle(dev, geometric=True):
+    return hsc.hsc_create(dev.n, dev.orb, dev.rowptr, dev.col, dev.val, dev.contact_ptr,
+                          dev.contact_sites, dev.dims if geometric else None)
+
+
+def test_rejects_non_symmetric_h():
+    dev = W.cubic_device((3, 3, 3), seed=0)
+    val = dev.val.copy()
+    val[1] += 0.5        # breaks H = H^T
+    with pytest.raises(hsc.HSCError) as ei:
+        hsc.hsc_create(dev.n, 1, dev.rowptr, dev.col, val, dev.contact_ptr, dev.contact_sites, dev.dims)
+    assert ei.value.code == hsc.HSC_ERR_NOT_SYMMETRIC
+
+
+def test_rejects_bad_arguments_and_state():
+    dev = W.cubic_device((3, 3, 3), seed=0)
+    with pytest.raises(hsc.HSCError) as ei:
+        hsc.hsc_create(dev.n, 1, dev.rowptr, dev.col, dev.val, dev.contact_ptr, dev.contact_sites,
+                       (3, 3, 4))
+    assert ei.value.code == hsc.HSC_ERR_ARG
+    h = _handle(dev)
+    sr, sl = W.self_energies(dev, 1)
+    out = np.zeros((1, dev.n), np.complex128)
+    with pytest.raises(hsc.HSCError) as ei:    # solve before analyze
+        hsc.hsc_solve(h, np.array([0.1]), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(), None, None)
+    assert ei.value.code == hsc.HSC_ERR_STATE
+    with pytest.raises(hsc.HSCError):
+        hsc.hsc_analyze(h, 0)
+    hsc.hsc_destroy(h)
+
+
+def _tree(dev, leaf, geometric=True):
+    h = _handle(dev, geometric)
+    st = hsc.hsc_analyze(h, leaf)
+    cl = [hsc.hsc_cluster(h, i) for i in range(st.n_clusters)]
+    hsc.hsc_destroy(h)
+    return st, cl
+
+
+@pytest.mark.parametrize("dims,orb,leaf,geo", [((8, 8, 8), 1, 4, True), ((9, 5, 7), 1, 3, True),
+                                               ((6, 3, 2), 3, 2, True), ((7, 6, 5), 1, 2, False),
+                                               ((17, 1, 1), 1, 1, True)])
+def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo):
+    """Every unknown is owned once; no H entry joins two unrelated clusters (separation); each U_i
+    is exactly the set of ancestor unknowns adjacent to the subtree of i (Section 2.2)."""
+    dev = W.cubic_device(dims, seed=1) if orb == 1 else W.wire_device(dims, orb=orb, seed=1)
+    st, cl = _tree(dev, leaf, geo)
+    nc = st.n_clusters
+    owner = np.full(dev.n, -1)
+    for i, (info, own, upd) in enumerate(cl):
+        assert np.all(owner[own] == -1)
+        owner[own] = i
+    assert np.all(owner >= 0)
+    parent = [info.parent for info, _, _ in cl]
+    assert parent[-1] == -1 and all(p > i for i, p in enumerate(parent[:-1]))
+    anc = [set() for _ in range(nc)]
+    for i in range(nc - 1, -1, -1):
+        if parent[i] >= 0:
+            anc[i] = anc[parent[i]] | {parent[i]}
+    sub = [set() for _ in range(nc)]
+    for i in range(nc):
+        sub[i].add(i)
+        for a in anc[i]:
+            sub[a].add(i)
+    H = dev.to_scipy().tocoo()
+    for a, b in zip(H.row, H.col):
+        ca, cb = owner[a], owner[b]
+        assert ca == cb or ca in anc[cb] or cb in anc[ca]
+    adj = [set() for _ in range(dev.n)]
+    for a, b in zip(H.row, H.col):
+        if a != b:
+            adj[a].add(b)
+    for i, (info, own, upd) in enumerate(cl):
+        dom = set(np.nonzero(np.isin(owner, list(sub[i])))[0])
+        boundary = set()
+        for u in dom:
+            boundary |= adj[u]
+        boundary -= dom
+        assert set(upd.tolist()) == boundary
+        assert all(owner[u] in anc[i] for u in upd)
+        assert info.m == len(upd) and info.n == len(own)
+        assert info.lesser == int(bool(np.isin(own, dev.contact_unknowns()).any()) or
+                                  any(cl[c][0].lesser for c in info.child if c >= 0))
+
+
+def test_operation_count_follows_table_1_cube_slope():
+    """Table 1: the HSC-extension costs O(N^6) on an N^3 cube; the model's log-log slope between
+    N = 24 and N = 48 (leaves <= 8) must be close to 6 (and far from RGF's 7)."""
+    f = []
+    Ns = [24, 32, 40, 48]
+    for N in Ns:
+        st, _ = _tree(W.cubic_device((N, N, N), seed=0), 8)
+        f.append(st.flops_gr + st.flops_gl)
+    slope = np.polyfit(np.log(Ns), np.log(f), 1)[0]
+    assert 5.3 < slope < 6.5, slope
+
+
+def test_degenerate_chain_tree():
+    """A 1D chain with leaves of one site: every cluster is one unknown and every update set has at
+    most two entries (the separator structure that makes HSC coincide with RGF, Section 2.2)."""
+    st, cl = _tree(W.chain_device(31), 1)
+    assert st.max_n == 1 and st.max_m <= 2

@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerance (normwise relative error ||x - x_ref||_inf / ||x_ref||_inf of every output vector at
+every energy: diag G^r, diag G^<, requested entries):
+
+* TOL = 1e-10 for the complex128 path wherever the block elimination of Algorithm 1 is well
+  conditioned. The elimination keeps the nested-dissection order and pivots only inside each
+  cluster block; for complex-symmetric A = B + iC with C = eta I + Gamma/2 positive definite, the
+  growth of such an elimination is bounded by about ||B|| / lambda_min(C) ~ ||H|| / eta. With
+  eta = 0.05 that is ~1e2 and every case below must agree to 1e-10 (any indexing or sign mistake
+  gives O(1) differences).
+* TOL_RESONANT = 1e-5 at the workloads' eta = 1e-6: there the growth bound is ~1e7 and an interior
+  cluster whose local level sits near E loses digits in *any* FP64 evaluation of the block steps
+  (a LAPACK evaluation of the same steps is off by 2.4e-7 and 3.9e-6 on two of the cases below).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1702_05167_gb300 import hsc, workloads as W
+from oracle import dense, rgf, columns
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+TOL_RESONANT = 1e-5
+ETA_WELL = 0.05
+
+
+def relerr(x, ref):
+    return np.abs(x - ref).max() / np.abs(ref).max()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hsc.load()
+
+
+def _dense_case(dev, leaf, energies, eta=ETA_WELL, f=(1.0, 0.0), pairs=None, tol=TOL):
+    sr, sl = W.self_energies(dev, len(energies), f)
+    s = hsc.Solver(dev, leaf)
+    dgr, dgl, pgr, pgl = s.solve(energies, eta, sr, sl, pairs=pairs)
+    Hd = dev.to_scipy().toarray()
+    for k, E in enumerate(energies):
+        G, Gl = dense.solve(Hd, E, eta, dev.contact_unknowns(), sr[k], sl[k])
+        assert relerr(dgr[k], np.diag(G)) <= tol
+        assert relerr(dgl[k], np.diag(Gl)) <= tol
+        if pairs is not None:
+            assert relerr(pgr[k], G[pairs[:, 0], pairs[:, 1]]) <= tol
+            assert relerr(pgl[k], Gl[pairs[:, 0], pairs[:, 1]]) <= tol
+    s.close()
+
+
+def test_tiny_8cube_matches_dense():
+    cfg = W.tiny()
+    _dense_case(cfg["dev"], cfg["leaf"], cfg["energies"], cfg["eta"], cfg["f"],
+                pairs=W.plane_pairs(cfg["dev"], 3))
+
+
+@pytest.mark.parametrize("dims,leaf,f", [((7, 5, 6), 2, (1.0, 0.3)), ((9, 4, 4), 3, (0.5, 1.0)),
+                                         ((5, 5, 5), 5, (1.0, 0.0)), ((12, 3, 2), 1, (1.0, 0.0))])
+def test_ragged_grids_several_energies(dims, leaf, f):
+    dev = W.cubic_device(dims, W=1.0, seed=sum(dims))
+    E = np.array([-2.9, -0.4, 0.0, 0.23, 1.3, 3.7])
+    _dense_case(dev, leaf, E, f=f, pairs=W.plane_pairs(dev, dims[0] // 2))
+    _dense_case(dev, leaf, E, eta=1e-6, f=f, pairs=W.plane_pairs(dev, dims[0] // 2), tol=TOL_RESONANT)
+
+
+def test_resonant_interior_block_matches_lapack_block_elimination_bound():
+    """At E = 0 the 7x5x6 grid (seed 18, leaves <= 2) has a 4-site interior leaf whose local level
+    sits within ~1e-4 of E; its block has cond ~1e4 and the fixed-order block elimination has element
+    growth, so no FP64 evaluation of Algorithm 1 reaches 1e-10 there (a LAPACK evaluation of the same
+    block steps is off by 2.4e-7). The GPU result must still be within TOL_RESONANT."""
+    dev = W.cubic_device((7, 5, 6), W=1.0, seed=18)
+    sr, sl = W.self_energies(dev, 1, (1.0, 0.3))
+    s = hsc.Solver(dev, 2)
+    dgr, dgl, _, _ = s.solve(np.array([0.0]), 1e-6, sr, sl)
+    s.close()
+    G, Gl = dense.solve(dev.to_scipy().toarray(), 0.0, 1e-6, dev.contact_unknowns(), sr[0], sl[0])
+    assert relerr(dgr[0], np.diag(G)) <= TOL_RESONANT
+    assert relerr(dgl[0], np.diag(Gl)) <= TOL_RESONANT
+
+
+def test_multi_orbital_wire():
+    dev = W.wire_device((6, 3, 2), orb=3, seed=2)
+    _dense_case(dev, 2, np.array([-1.0, 0.1, 2.0]), pairs=W.plane_pairs(dev, 2))
+
+
+def test_chain_degenerate_tree():
+    """A 1D chain: every separator is one site; the tree degenerates towards RGF."""
+    dev = W.chain_device(23, eps=np.linspace(-0.3, 0.3, 23))
+    _dense_case(dev, 1, np.array([-1.5, 0.2, 1.9]), pairs=np.array([[4, 5], [11, 12], [0, 1]]))
+
+
+def test_general_graph_bisection():
+    dev = W.cubic_device((6, 5, 4), W=1.0, seed=11)
+    sr, sl = W.self_energies(dev, 2)
+    s = hsc.Solver(dev, 2, geometric=False)
+    E = np.array([0.2, -1.1])
+    dgr, dgl, _, _ = s.solve(E, ETA_WELL, sr, sl)
+    Hd = dev.to_scipy().toarray()
+    for k in range(2):
+        G, Gl = dense.solve(Hd, E[k], ETA_WELL, dev.contact_unknowns(), sr[k], sl[k])
+        assert relerr(dgr[k], np.diag(G)) <= TOL and relerr(dgl[k], np.diag(Gl)) <= TOL
+    s.close()
+
+
+def test_waves_and_device_io_agree():
+    """Energies split into several workspace waves, and device-resident io, give the same bits as
+    one host-io call."""
+    import torch
+    dev = W.cubic_device((8, 6, 5), W=1.0, seed=3)
+    E = np.linspace(-3, 3, 11)
+    sr, sl = W.self_energies(dev, len(E))
+    s = hsc.Solver(dev, 3)
+    a = s.solve(E, 1e-6, sr, sl)
+    per = s.stats.bytes_per_energy
+    os.environ["HSC_WORKSPACE_GB"] = str(3.5 * per / 2**30)
+    try:
+        s2 = hsc.Solver(dev, 3)
+        b = s2.solve(E, 1e-6, sr, sl)
+        s2.close()
+    finally:
+        del os.environ["HSC_WORKSPACE_GB"]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    dv = torch.device("cuda:0")
+    tE = torch.from_numpy(E).to(dv)
+    tsr = torch.from_numpy(sr.view(np.float64)).to(dv)
+    tsl = torch.from_numpy(sl.view(np.float64)).to(dv)
+    ogr = torch.zeros((len(E), dev.n * 2), dtype=torch.float64, device=dv)
+    ogl = torch.zeros_like(ogr)
+    hsc.hsc_solve(s.h, tE, 1e-6, tsr, tsl, hsc.HSC_FP64, None, ogr, ogl, None, None,
+                  stream=torch.cuda.current_stream().cuda_stream, io_on_device=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ogr.cpu().numpy().view(np.complex128), a[0])
+    np.testing.assert_array_equal(ogl.cpu().numpy().view(np.complex128), a[1])
+    s.close()
+
+
+def test_without_lesser_self_energy():
+    dev = W.cubic_device((6, 6, 6), W=1.0, seed=4)
+    E = np.array([0.7])
+    sr, sl = W.self_energies(dev, 1)
+    s = hsc.Solver(dev, 3)
+    dgr, dgl, _, _ = s.solve(E, ETA_WELL, sr, None)
+    assert dgl is None
+    G, _ = dense.solve(dev.to_scipy().toarray(), E[0], ETA_WELL, dev.contact_unknowns(), sr[0], sl[0])
+    assert relerr(dgr[0], np.diag(G)) <= TOL
+    s.close()
+
+
+def test_errors_are_reported():
+    dev = W.cubic_device((4, 4, 4), seed=1)
+    s = hsc.Solver(dev, 2)
+    sr, sl = W.self_energies(dev, 1)
+    with pytest.raises(hsc.HSCError) as ei:
+        s.solve(np.array([0.1]), 1e-6, sr, sl, pairs=np.array([[0, 63]]))   # opposite corners
+    assert ei.value.code == hsc.HSC_ERR_NOT_SELECTED
+    s.close()
+
+
+def test_mid_32cube_sampled_against_rgf():
+    """The metric workload (32^3, 64 energies, leaves 8^3) in the launch configuration the
+    benchmark times; two energies checked in full against the RGF oracle, and sampled sites at
+    four more energies against single-column sparse solves."""
+    cfg = W.mid()
+    dev = cfg["dev"]
+    E = cfg["energies"]
+    sr, sl = W.self_energies(dev, len(E), cfg["f"])
+    s = hsc.Solver(dev, cfg["leaf"])
+    dgr, dgl, pgr, pgl = s.solve(E, cfg["eta"], sr, sl, pairs=cfg["pairs"])
+    s.close()
+    H = dev.to_scipy()
+    Ls = 32 * 32
+    u, v = cfg["pairs"][:, 0] - 15 * Ls, cfg["pairs"][:, 1] - 16 * Ls
+    for k in (9, 40):
+        out = rgf.sweep(H, Ls, E[k], cfg["eta"], dev.contact_unknowns(), sr[k], sl[k],
+                        coupling_layers=(15,))
+        errs = [relerr(dgr[k], out["diag_gr"]), relerr(dgl[k], out["diag_gl"]),
+                relerr(pgr[k], out["coupling_gr"][15][u, v]),
+                relerr(pgl[k], out["coupling_gl"][15][u, v])]
+        print(f"32^3 E={E[k]:+.4f} vs RGF: diag Gr {errs[0]:.2e} diag Gl {errs[1]:.2e} "
+              f"Gr(15,16) {errs[2]:.2e} Gl(15,16) {errs[3]:.2e}")
+        assert max(errs) <= TOL_RESONANT
+    rng = np.random.default_rng(5)
+    rows = rng.choice(dev.n, 6, replace=False)
+    for k in (0, 21, 52, 63):
+        gr, gl, _ = columns.sampled(H, E[k], cfg["eta"], dev.contact_unknowns(), sr[k], sl[k], rows)
+        e1 = np.abs(dgr[k][rows] - gr).max() / np.abs(dgr[k]).max()
+        e2 = np.abs(dgl[k][rows] - gl).max() / np.abs(dgl[k]).max()
+        print(f"32^3 E={E[k]:+.4f} sampled vs sparse LU: Gr {e1:.2e} Gl {e2:.2e}")
+        assert max(e1, e2) <= TOL_RESONANT
+
+
+def test_mid_32cube_well_conditioned_full_parity():
+    """The 32^3 grid and leaves 8^3 at eta = 0.05 (bounded growth): full diag G^r, diag G^< and the
+    plane-15/16 coupling blocks against the RGF oracle at 1e-10."""
+    cfg = W.mid()
+    dev = cfg["dev"]
+    E = np.array([-3.3, 0.41])
+    sr, sl = W.self_energies(dev, len(E), cfg["f"])
+    s = hsc.Solver(dev, cfg["leaf"])
+    dgr, dgl, pgr, pgl = s.solve(E, ETA_WELL, sr, sl, pairs=cfg["pairs"])
+    s.close()
+    Ls = 32 * 32
+    u, v = cfg["pairs"][:, 0] - 15 * Ls, cfg["pairs"][:, 1] - 16 * Ls
+    for k in range(len(E)):
+        out = rgf.sweep(dev.to_scipy(), Ls, E[k], ETA_WELL, dev.contact_unknowns(), sr[k], sl[k],
+                        coupling_layers=(15,))
+        assert relerr(dgr[k], out["diag_gr"]) <= TOL
+        assert relerr(dgl[k], out["diag_gl"]) <= TOL
+        assert relerr(pgr[k], out["coupling_gr"][15][u, v]) <= TOL
+        assert relerr(pgl[k], out["coupling_gl"][15][u, v]) <= TOL
