@@ -149,6 +149,23 @@ int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int32_t* n_out)
  *   Errors: HSC_ERR_ARG, HSC_ERR_CUDA, HSC_ERR_OOM. */
 int hsc_device_fp64_peaks(double* dmma_gflops, double* dfma_gflops);
 
+/* hsc_block_inverse_noalloc -- invert `batch` dense n x n complex128 blocks without allocating.
+ *   The paper has no counterpart: this is a deployment variant of the Gauss-Jordan block inversion
+ *   (partial pivoting inside each block) that hsc_solve uses for the cluster blocks, for callers
+ *   that cannot allocate device memory while they run (their memory pool already holds the free
+ *   device memory, or cudaMalloc/cudaFree's implicit synchronisation is not acceptable).
+ *   A     device, batch blocks of n x n, row-major, contiguous (read only unless A == Ainv)
+ *   Ainv  device, same layout, receives the inverses (may equal A: in place)
+ *   cuda_stream  stream to run on (NULL: legacy default stream); the call synchronises it.
+ *   Limits: n <= 1024, batch <= 256, n * batch <= 8192. Scratch lives in one fixed 4.3 MiB device
+ *   array per device (held until process exit); no cudaMalloc/cudaFree is called. The first call on
+ *   a device looks up that array's address (cudaGetSymbolAddress) and should come before any stream
+ *   capture. Calls whose work overlaps on the GPU race on the shared array: serialise them.
+ *   Errors: HSC_ERR_ARG (sizes beyond the limits, NULL pointers), HSC_ERR_SINGULAR (zero pivot),
+ *   HSC_ERR_CUDA. */
+int hsc_block_inverse_noalloc(int32_t n, int32_t batch, const hsc_c128* A, hsc_c128* Ainv,
+                              void* cuda_stream);
+
 /* hsc_last_error -- text of the last failure on this handle ("" if none); valid until the next
  * call on the handle. Accepts NULL (returns the last global error, e.g. from hsc_create). */
 const char* hsc_last_error(hsc_t h);

@@ -172,6 +172,17 @@ def hsc_device_fp64_peaks():
     return a.value, b.value
 
 
+def hsc_block_inverse_noalloc(n, batch, A, Ainv, stream=None):
+    """Invert `batch` n x n complex128 device blocks (torch float64 tensors holding interleaved
+    re/im) with the library's allocation-free entry point."""
+    L = load()
+    L.hsc_block_inverse_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]
+    L.hsc_block_inverse_noalloc.restype = ctypes.c_int
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(None, L.hsc_block_inverse_noalloc(int(n), int(batch), _ptr(A), _ptr(Ainv), s))
+
+
 def hsc_last_error(h=None):
     return load().hsc_last_error(h).decode(errors="replace")
 
