@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--impl", default="hsc", choices=["hsc", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E"],
+                   help="cubic32: the metric workload; cubic24x8E: 24^3 grid, 8 energies (a few GB, "
+                        "for ncu captures)")
     return p.parse_args()
 
 
@@ -100,9 +103,13 @@ def dist():
     return ws, rank, local
 
 
-def workload(rank, ws):
+def workload(rank, ws, name="cubic32"):
     from paper_1702_05167_gb300 import workloads as W
     cfg = W.mid()
+    if name == "cubic24x8E":
+        dev = W.cubic_device((24, 24, 24), t=-1.0, W=1.0, seed=0, gamma=0.5)
+        cfg = dict(name="cubic_24x24x24_8E", dev=dev, energies=np.linspace(-5.5, 5.5, 8), eta=1e-6,
+                   leaf=8, f=(1.0, 0.0), pairs=W.plane_pairs(dev, 11))
     E = cfg["energies"]
     if ws > 1:   # interleaved sub-grids: rank r shifts the grid by r/ws of a spacing
         E = E + (E[1] - E[0]) * rank / ws
@@ -159,7 +166,7 @@ def run_hsc(args):
         tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dvc = torch.device("cuda", local)
-    cfg = workload(rank, ws)
+    cfg = workload(rank, ws, args.workload)
     dev = cfg["dev"]
     E = cfg["energies"]
     nE = len(E)
@@ -273,7 +280,7 @@ def run_hsc(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-                "config": {"workload": "cubic_32x32x32_64E", "grid": [32, 32, 32],
+                "config": {"workload": cfg["name"], "grid": list(dev.dims),
                            "energies_per_gpu": nE, "eta": cfg["eta"], "leaf_max": cfg["leaf"],
                            "precision": "complex128 (HSC_FP64)", "io": "device-resident",
                            "clusters": st.n_clusters,

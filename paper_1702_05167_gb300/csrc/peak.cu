@@ -9,7 +9,9 @@ constexpr int ITERS = 2048;
 
 __global__ void k_probe_dmma(double* out) {
   double a = 1.0 + threadIdx.x * 1e-9, b = 1.0 - threadIdx.x * 1e-9;
-  double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double c[8];   // distinct starting values: no two accumulator chains are identical
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = 1e-3 * (k + 1) + 1e-12 * threadIdx.x;
   for (int i = 0; i < ITERS; ++i) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
