@@ -96,7 +96,13 @@ int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* own, int32_
  *   E[n_E]                energies (eV); eta (eV) > 0 recommended (eta = 0 may be singular)
  *   sigma_r[n_E][n_cs]    diagonal Sigma^r on the n_cs contact slots, per energy
  *   sigma_less[n_E][n_cs] diagonal Sigma^< per energy, or NULL: G^< work and outputs are skipped
- *   precision             HSC_FP64 (complex128 throughout) or HSC_MIXED
+ *   precision             HSC_FP64: complex128 storage, every block product on the FP64 pipe.
+ *                         HSC_MIXED: complex128 storage; block products below the top tree levels
+ *                         (HSC_FP64_LEVELS, default 2: the root and its children stay FP64) run on
+ *                         the tensor cores as 3xTF32 split products with FP32 accumulation
+ *                         (~1e-6 relative per product). Cluster inverses keep FP64 panels
+ *                         (HSC_MIXED_GJ_FP64=1 also keeps their trailing updates on the FP64 pipe).
+ *                         Accuracy degrades with the elimination's growth (~||H||/eta).
  *   n_req, req_pairs[n_req][2]  user-order unknown pairs (a, b) whose G^r_ab (and G^<_ab) are
  *                         returned; every pair must be in the filled pattern
  *   diag_gr[n_E][n]       out: G^r_uu;            diag_gl[n_E][n] out: G^<_uu (ignored if

@@ -41,8 +41,9 @@ struct GemmArgs {
   double flops;                   // algorithmic real flops per energy (host bookkeeping)
 };
 
-// launchers (gemm_f64.cu)
+// launchers (gemm_f64.cu, gemm_tc.cu)
 cudaError_t gemm_z(const GemmArgs& g, int n_energy, cudaStream_t s);
+cudaError_t gemm_tc(const GemmArgs& g, int n_energy, int* flag, cudaStream_t s);
 
 // Gauss-Jordan inversion problem: n x n matrix at element offset `off` (row stride ld) of a
 // per-energy array; pivots at piv_off of the per-energy pivot array; panel copy M (n x nb, row

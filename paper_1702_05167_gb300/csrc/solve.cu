@@ -24,6 +24,11 @@
 
 namespace hsc {
 
+struct GemmPair {
+  GemmArgs z;    // 64x64 tiles, FP64 tensor pipe (gemm_z)
+  GemmArgs tc;   // 128x128 tiles, tcgen05 3xTF32 (gemm_tc)
+};
+
 struct UpLevel {
   int nl = 0;
   int64_t lc = 0;           // index into the LevelCluster array
@@ -31,10 +36,10 @@ struct UpLevel {
   double asm_bytes = 0, gather_bytes = 0;   // algorithmic bytes per energy
   int max_n = 0;
   bool any_lesser = false;
-  GemmArgs u1{}, u2{}, u3{}, u4{};
+  GemmPair u1{}, u2{}, u3{}, u4{};
   int64_t gj = 0;           // index into the GJProb array
   int nmat = 0;
-  std::vector<GemmArgs> steps;
+  std::vector<GemmPair> steps;
 };
 
 struct DownLevel {
@@ -43,12 +48,12 @@ struct DownLevel {
   int64_t max_sq = 0;
   bool any_lesser = false;
   double gather_bytes = 0;
-  GemmArgs d[9]{};
+  GemmPair d[9]{};
 };
 
-enum KClass { K_GEMM = 0, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
+enum KClass { K_GEMM = 0, K_GEMM_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
               K_OUT, K_NCLASS };
-static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gj_panel", "gj_swap", "gj_colperm",
+static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
                                            "assemble", "add_a", "lesser_fold", "gather", "out"};
 
 struct Prof {
@@ -65,11 +70,14 @@ struct DeviceState {
   Prof prof;
   bool planned = false;
   int nb = 16;                       // Gauss-Jordan panel width
+  int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
+  bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
   // energy-independent device arrays
   ClusterGlobal* cg = nullptr;
   LevelCluster* lcs = nullptr;
   GJProb* gjp = nullptr;
   GemmProb* gp = nullptr;
+  GemmProb* gp128 = nullptr;
   int32_t *maps = nullptr, *h_rq = nullptr, *own_contact = nullptr;
   int64_t *h_vi = nullptr, *doff = nullptr;
   c64* hval = nullptr;
@@ -127,37 +135,50 @@ cudaError_t upload(DeviceState* d, T** dst, const std::vector<T>& v) {
 constexpr int TILE = 64;
 
 struct GemmList {
-  std::vector<GemmProb>& all;
-  size_t start;
-  int tiles = 0;
+  std::vector<GemmProb>& all;      // 64x64-tile problem lists
+  std::vector<GemmProb>& all128;   // 128x128-tile problem lists
+  size_t start, start128;
+  int tiles = 0, tiles128 = 0;
   int count = 0;
   double flops = 0;
-  explicit GemmList(std::vector<GemmProb>& a) : all(a), start(a.size()) {}
+  GemmList(std::vector<GemmProb>& a, std::vector<GemmProb>& b)
+      : all(a), all128(b), start(a.size()), start128(b.size()) {}
   void add(int M, int N, int K, int64_t a, int lda, int64_t b, int ldb, int64_t c, int ldc,
            int64_t dd = 0, int ldd = 0, int use_d = 0, int zr0 = 0, int zr1 = 0) {
     if (M <= 0 || N <= 0) return;
-    if (all.size() != start + (size_t)count) throw std::logic_error("interleaved GEMM lists");
+    if (all.size() != start + (size_t)count || all128.size() != start128 + (size_t)count)
+      throw std::logic_error("interleaved GEMM lists");
     ++count;
     GemmProb p{};
     p.M = M; p.N = N; p.K = K;
     p.a = a; p.lda = lda; p.b = b; p.ldb = ldb; p.c = c; p.ldc = ldc; p.d = dd; p.ldd = ldd;
     p.use_d = use_d; p.zr0 = zr0; p.zr1 = zr1;
+    GemmProb q = p;
     p.tiles_n = (N + TILE - 1) / TILE;
     p.tile_start = tiles;
-    flops += 8.0 * M * N * K;
     tiles += ((M + TILE - 1) / TILE) * p.tiles_n;
+    q.tiles_n = (N + 127) / 128;
+    q.tile_start = tiles128;
+    tiles128 += ((M + 127) / 128) * q.tiles_n;
+    flops += 8.0 * M * N * K;
     all.push_back(p);
+    all128.push_back(q);
   }
-  // records the list in a GemmArgs; the device pointer is patched after upload
-  GemmArgs args(int opa, int opb, double ar, double ai, double br, double bi) const {
+  // records the lists; device pointers are patched after upload (index stored in probs)
+  GemmPair args(int opa, int opb, double ar, double ai, double br, double bi) const {
+    GemmPair r{};
     GemmArgs g{};
-    g.probs = reinterpret_cast<const GemmProb*>(start);   // index, patched later
-    g.nprob = (int)(all.size() - start);
-    g.total_tiles = tiles;
+    g.nprob = count;
     g.opa = opa; g.opb = opb;
     g.ar = ar; g.ai = ai; g.br = br; g.bi = bi;
     g.flops = flops;
-    return g;
+    r.z = g;
+    r.z.probs = reinterpret_cast<const GemmProb*>(start);
+    r.z.total_tiles = tiles;
+    r.tc = g;
+    r.tc.probs = reinterpret_cast<const GemmProb*>(start128);
+    r.tc.total_tiles = tiles128;
+    return r;
   }
 };
 
@@ -182,7 +203,7 @@ int build_schedule(hsc_ctx* h) {
 
   std::vector<LevelCluster> lcs;
   std::vector<GJProb> gjs;
-  std::vector<GemmProb> gps;
+  std::vector<GemmProb> gps, gps128;
   int64_t tt_max = 1, tz_max = 1, tn_max = 1, gjt_max = 1;
 
   auto base_lc = [&](int i) {
@@ -239,26 +260,26 @@ int build_schedule(hsc_ctx* h) {
     U.nmat = U.nl;
     const LevelCluster* lv = lcs.data() + U.lc;
     {
-      GemmList g1(gps);
+      GemmList g1(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         g1.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.x, L.m);
       }
       U.u1 = g1.args(OP_N, OP_N, 1, 0, 0, 0);
-      GemmList g2(gps);
+      GemmList g2(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         g2.add(L.m, L.m, L.n, L.aug + L.n, L.n + L.m, L.x, L.m, L.sq, L.m, L.sq, L.m, 1);
       }
       U.u2 = g2.args(OP_T, OP_N, -1, 0, 1, 0);
-      GemmList g3(gps);
+      GemmList g3(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         if (L.lesser)
           g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.x, L.m, L.tt, L.m, L.aug + L.n, L.n + L.m, 1);
       }
       U.u3 = g3.args(OP_N, OP_C, 0.5, 0, -1, 0);
-      GemmList g4(gps);
+      GemmList g4(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         if (L.lesser) g4.add(L.m, L.m, L.n, L.x, L.m, L.tt, L.m, L.tz, L.m);
@@ -266,7 +287,7 @@ int build_schedule(hsc_ctx* h) {
       U.u4 = g4.args(OP_T, OP_N, 1, 0, 0, 0);
       const GJProb* gl = gjs.data() + U.gj;
       for (int k0 = 0; k0 < U.max_n; k0 += nb) {
-        GemmList gs(gps);
+        GemmList gs(gps, gps128);
         for (int k = 0; k < U.nl; ++k) {
           const GJProb& q = gl[k];
           if (q.n <= k0) continue;
@@ -299,57 +320,57 @@ int build_schedule(hsc_ctx* h) {
     tz_max = std::max(tz_max, tz);
     tn_max = std::max(tn_max, tn);
     const LevelCluster* lv = lcs.data() + D.lc;
-    GemmList g1(gps);
+    GemmList g1(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g1.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m);
     }
     D.d[0] = g1.args(OP_N, OP_N, -1, 0, 0, 0);
-    GemmList g2(gps);
+    GemmList g2(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g2.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, 1);
     }
     D.d[1] = g2.args(OP_N, OP_T, -1, 0, 1, 0);
-    GemmList g3(gps);
+    GemmList g3(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser) g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn + L.n, L.n + L.m);
     }
     D.d[2] = g3.args(OP_N, OP_C, 1, 0, 0, 0);
-    GemmList g4(gps);
+    GemmList g4(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser)
         g4.add(L.n, L.m, L.m, L.aug + L.n, L.n + L.m, L.tz, L.m, L.tn + L.n, L.n + L.m, L.tn + L.n, L.n + L.m, 1);
     }
     D.d[3] = g4.args(OP_N, OP_C, 1, 0, 1, 0);
-    GemmList g5(gps);
+    GemmList g5(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser) g5.add(L.n, L.n, L.n, L.aug, L.n + L.m, L.aug, L.n + L.m, L.tn, L.n + L.m);
     }
     D.d[4] = g5.args(OP_N, OP_C, 1, 0, 0, 0);
-    GemmList g6(gps);
+    GemmList g6(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser)
         g6.add(L.n, L.n, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn, L.n + L.m, L.tn, L.n + L.m, 1);
     }
     D.d[5] = g6.args(OP_N, OP_H, 1, 0, 1, 0);
-    GemmList g7(gps);
+    GemmList g7(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser) g7.add(L.n, L.n + L.m, L.n, L.aug, L.n + L.m, L.tn, L.n + L.m, L.aug, L.n + L.m);
     }
     D.d[6] = g7.args(OP_N, OP_N, 1, 0, 0, 0);
-    GemmList g8(gps);
+    GemmList g8(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g8.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.lesser);
     }
     D.d[7] = g8.args(OP_N, OP_N, -1, 0, 1, 0);
-    GemmList g9(gps);
+    GemmList g9(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g9.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, L.lesser);
@@ -377,6 +398,7 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->lcs, lcs);
   UP(&d->gjp, gjs);
   UP(&d->gp, gps);
+  UP(&d->gp128, gps128);
   UP(&d->maps, P.map_child);
   UP(&d->h_rq, P.h_rq);
   UP(&d->h_vi, P.h_vi);
@@ -392,7 +414,10 @@ int build_schedule(hsc_ctx* h) {
     return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc flag");
   d->fixed.push_back(d->flag);
   // patch problem-list pointers
-  auto patch = [&](GemmArgs& g) { g.probs = d->gp + reinterpret_cast<size_t>(g.probs); };
+  auto patch = [&](GemmPair& g) {
+    g.z.probs = d->gp + reinterpret_cast<size_t>(g.z.probs);
+    g.tc.probs = d->gp128 + reinterpret_cast<size_t>(g.tc.probs);
+  };
   for (auto& U : d->up) {
     patch(U.u1); patch(U.u2); patch(U.u3); patch(U.u4);
     for (auto& s : U.steps) patch(s);
@@ -484,18 +509,27 @@ cudaError_t prof_stop(DeviceState* d, cudaStream_t s, int cls, int nk, double fl
 // One wave of `ne` energies with inputs already on the device.
 int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, const c64* sl,
              int64_t npair, const int64_t* poff, c64* ogr, c64* ogl, c64* pgr, c64* pgl,
-             cudaStream_t s) {
+             int precision, cudaStream_t s) {
   DeviceState* d = h->dev;
   const bool les = sl != nullptr;
   const int64_t ncs = h->n_contact_unknowns;
   // ---- upward (Algorithm 1 first loop, Algorithm 2 fold) ----
-  auto gemm = [&](const GemmArgs& g) -> int {
-    if (g.total_tiles <= 0) return HSC_OK;
-    LAUNCH(K_GEMM, 1, g.flops * ne, 0.0, gemm_z(g, ne, s));
+  bool tc = false;   // current level's GEMMs on the tensor cores (mixed mode, below the top levels)
+  auto gemm = [&](const GemmArgs& gz, const GemmArgs& gt) -> int {
+    if (gz.total_tiles <= 0) return HSC_OK;
+    if (tc) LAUNCH(K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
+    else LAUNCH(K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s));
     return HSC_OK;
   };
-#define GEMM(g) do { int _r = gemm(g); if (_r != HSC_OK) return _r; } while (0)
-  for (auto& U : d->up) {
+#define GEMM(pair, ...)                                                   \
+  do {                                                                    \
+    int _r = gemm(bind((pair).z, __VA_ARGS__), bind((pair).tc, __VA_ARGS__)); \
+    if (_r != HSC_OK) return _r;                                          \
+  } while (0)
+  const int nup = (int)d->up.size();
+  for (int hl = 0; hl < nup; ++hl) {
+    auto& U = d->up[hl];
+    tc = precision == HSC_MIXED && hl < nup - d->fp64_levels;
     const LevelCluster* lc = d->lcs + U.lc;
     LAUNCH(K_ASSEMBLE, 1, 0.0, U.asm_bytes * ne,
            launch_assemble(lc, U.nl, U.total, d->cg, d->maps, d->F, d->S, d->L, d->LS, d->aug_es,
@@ -513,38 +547,44 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
              launch_gj_swap(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
                             d->gjt_es, k0, d->nb, ne, s));
-      GEMM(bind(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es));
+      const bool keep = tc;
+      tc = tc && !d->gj_fp64;
+      GEMM(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es);
+      tc = keep;
     }
     LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
            launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s));
-    GEMM(bind(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0));
-    GEMM(bind(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es));
+    GEMM(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0);
+    GEMM(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es);
     if (les && U.any_lesser) {
-      GEMM(bind(U.u3, d->L, d->aug_es, d->X, d->x_es, d->T, d->tt_es, d->L, d->aug_es));
-      GEMM(bind(U.u4, d->X, d->x_es, d->T, d->tt_es, d->Z, d->tz_es, nullptr, 0));
+      GEMM(U.u3, d->L, d->aug_es, d->X, d->x_es, d->T, d->tt_es, d->L, d->aug_es);
+      GEMM(U.u4, d->X, d->x_es, d->T, d->tt_es, d->Z, d->tz_es, nullptr, 0);
       LAUNCH(K_FOLD, 1, 0.0, 0.0, launch_fold(lc, U.nl, U.max_sq, d->LS, d->sq_es, d->Z, d->tz_es, ne, s));
     }
   }
   // ---- downward (Algorithm 1 second loop, Algorithm 2 second loop) ----
-  for (auto& D : d->down) {
+  const int ndown = (int)d->down.size();
+  for (int dl = 0; dl < ndown; ++dl) {
+    auto& D = d->down[dl];
+    tc = precision == HSC_MIXED && dl >= d->fp64_levels;
     const LevelCluster* lc = d->lcs + D.lc;
     if (D.max_sq > 0)
       LAUNCH(K_GATHER, 1, 0.0, D.gather_bytes * ne * (les ? 1.0 : 0.5),
              launch_gather(lc, D.nl, D.max_sq, d->cg, d->u_owner, d->u_local, d->u_seg, d->posmap,
                            d->G, d->P, d->aug_es, d->GUU, les ? d->PUU : nullptr, d->tz_es, ne,
                            d->flag + 1, s));
-    GEMM(bind(D.d[0], d->X, d->x_es, d->GUU, d->tz_es, d->G, d->aug_es, nullptr, 0));
-    GEMM(bind(D.d[1], d->X, d->x_es, d->G, d->aug_es, d->G, d->aug_es, d->F, d->aug_es));
+    GEMM(D.d[0], d->X, d->x_es, d->GUU, d->tz_es, d->G, d->aug_es, nullptr, 0);
+    GEMM(D.d[1], d->X, d->x_es, d->G, d->aug_es, d->G, d->aug_es, d->F, d->aug_es);
     if (!les) continue;
     if (D.any_lesser) {
-      GEMM(bind(D.d[2], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0));
-      GEMM(bind(D.d[3], d->L, d->aug_es, d->GUU, d->tz_es, d->N, d->tn_es, d->N, d->tn_es));
-      GEMM(bind(D.d[4], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0));
-      GEMM(bind(D.d[5], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, d->N, d->tn_es));
-      GEMM(bind(D.d[6], d->F, d->aug_es, d->N, d->tn_es, d->P, d->aug_es, nullptr, 0));
+      GEMM(D.d[2], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0);
+      GEMM(D.d[3], d->L, d->aug_es, d->GUU, d->tz_es, d->N, d->tn_es, d->N, d->tn_es);
+      GEMM(D.d[4], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, nullptr, 0);
+      GEMM(D.d[5], d->L, d->aug_es, d->G, d->aug_es, d->N, d->tn_es, d->N, d->tn_es);
+      GEMM(D.d[6], d->F, d->aug_es, d->N, d->tn_es, d->P, d->aug_es, nullptr, 0);
     }
-    GEMM(bind(D.d[7], d->X, d->x_es, d->PUU, d->tz_es, d->P, d->aug_es, d->P, d->aug_es));
-    GEMM(bind(D.d[8], d->X, d->x_es, d->P, d->aug_es, d->P, d->aug_es, d->P, d->aug_es));
+    GEMM(D.d[7], d->X, d->x_es, d->PUU, d->tz_es, d->P, d->aug_es, d->P, d->aug_es);
+    GEMM(D.d[8], d->X, d->x_es, d->P, d->aug_es, d->P, d->aug_es, d->P, d->aug_es);
   }
 #undef GEMM
   LAUNCH(K_OUT, npair > 0 ? 2 : 1, 0.0, 32.0 * (double)(h->n + npair) * ne * (les ? 2 : 1),
@@ -620,7 +660,8 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
   if (h->n_contact_unknowns > 0 && !sigma_r) return hsc_fail(h, HSC_ERR_ARG, "sigma_r is NULL");
   if (n_req < 0 || (n_req > 0 && (!req_pairs || !req_gr || (sigma_less && !req_gl))))
     return hsc_fail(h, HSC_ERR_ARG, "bad requested-pair arrays");
-  if (precision != HSC_FP64) return hsc_fail(h, HSC_ERR_ARG, "precision must be HSC_FP64");
+  if (precision != HSC_FP64 && precision != HSC_MIXED)
+    return hsc_fail(h, HSC_ERR_ARG, "precision must be HSC_FP64 or HSC_MIXED");
   if (!(eta >= 0.0)) return hsc_fail(h, HSC_ERR_ARG, "eta must be >= 0");
   const Plan& P = h->plan;
   std::vector<int64_t> poff(n_req);
@@ -637,6 +678,8 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     CK(cudaGetDevice(&h->dev->device));
   }
   DeviceState* d = h->dev;
+  if (const char* v = getenv("HSC_FP64_LEVELS")) d->fp64_levels = atoi(v);
+  if (const char* v = getenv("HSC_MIXED_GJ_FP64")) d->gj_fp64 = atoi(v) != 0;
   int cur = 0;
   CK(cudaGetDevice(&cur));
   if (cur != d->device) return hsc_fail(h, HSC_ERR_ARG, "current device differs from the handle's device");
@@ -709,7 +752,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
       dE = sE; dsr = ssr; dsl = sigma_less ? ssl : nullptr;
       ogr = sgr; ogl = sgl; pgr = spr; pgl = spl;
     }
-    rc = run_wave(h, ne, dE, eta, dsr, dsl, n_req, d_poff, ogr, ogl, pgr, pgl, s);
+    rc = run_wave(h, ne, dE, eta, dsr, dsl, n_req, d_poff, ogr, ogl, pgr, pgl, precision, s);
     if (rc != HSC_OK) return rc;
     if (!io_on_device) {
       CK(cudaMemcpyAsync(diag_gr + e0 * n, sgr, ne * n * 16, cudaMemcpyDeviceToHost, s));
@@ -725,6 +768,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
   CK(cudaMemcpyAsync(flags, d->flag, sizeof(flags), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (flags[1]) return hsc_fail(h, HSC_ERR_ARG, "internal gather map error");
+  if (flags[2]) return hsc_fail(h, HSC_ERR_TIMEOUT, "a tensor-core GEMM wait expired");
   if (flags[0]) return hsc_fail(h, HSC_ERR_SINGULAR, "zero pivot in a cluster block");
   h->err.clear();
   return HSC_OK;
@@ -805,5 +849,40 @@ extern "C" int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int3
     out[p.cls[k]].bytes += p.bytes[k];
   }
   for (int c = 0; c < K_NCLASS; ++c) out[c].launches = p.launches[c];
+  return HSC_OK;
+}
+
+extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t M, int32_t N, int32_t K,
+                              const hsc_c128* A, int32_t lda, const hsc_c128* B, int32_t ldb,
+                              hsc_c128* C, int32_t ldc, const hsc_c128* D, int32_t ldd,
+                              double ar, double ai, double br, double bi, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || opa < 0 || opa > 3 || opb < 0 || opb > 3)
+    return hsc_fail(nullptr, HSC_ERR_ARG, "bad GEMM arguments");
+  GemmProb p{};
+  p.M = M; p.N = N; p.K = K;
+  p.lda = lda; p.ldb = ldb; p.ldc = ldc; p.ldd = ldd;
+  p.use_d = D ? 1 : 0;
+  const int tile = engine == 1 ? 128 : TILE;
+  p.tiles_n = (N + tile - 1) / tile;
+  p.tile_start = 0;
+  GemmProb* dp = nullptr;
+  int* flag = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMalloc(&dp, sizeof(GemmProb)) != cudaSuccess || cudaMalloc(&flag, sizeof(int)) != cudaSuccess)
+    return hsc_fail(nullptr, HSC_ERR_OOM, "cudaMalloc");
+  cudaMemcpy(dp, &p, sizeof(p), cudaMemcpyHostToDevice);
+  cudaMemset(flag, 0, sizeof(int));
+  GemmArgs g{};
+  g.probs = dp; g.nprob = 1; g.total_tiles = ((M + tile - 1) / tile) * p.tiles_n;
+  g.A = A; g.B = B; g.C = C; g.D = D;
+  g.ar = ar; g.ai = ai; g.br = br; g.bi = bi; g.opa = opa; g.opb = opb;
+  cudaError_t e = engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s);
+  int hf = 0;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dp);
+  cudaFree(flag);
+  if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, cudaGetErrorString(e));
+  if (hf) return hsc_fail(nullptr, HSC_ERR_TIMEOUT, "tensor-core GEMM wait expired");
   return HSC_OK;
 }

@@ -215,3 +215,20 @@ def test_mid_32cube_well_conditioned_full_parity():
         assert relerr(dgl[k], out["diag_gl"]) <= TOL
         assert relerr(pgr[k], out["coupling_gr"][15][u, v]) <= TOL
         assert relerr(pgl[k], out["coupling_gl"][15][u, v]) <= TOL
+
+
+def test_mixed_precision_bounded_growth():
+    """HSC_MIXED (3xTF32 tensor-core products, FP32 accumulation, FP64 top levels) on a grid with
+    bounded elimination growth (eta = 0.05): measured ~1e-5..1e-3 normwise; asserted at 5e-3. At
+    the workloads' eta = 1e-6 the growth (~1e7) makes FP32-level products useless (see DESIGN)."""
+    dev = W.cubic_device((12, 10, 8), W=1.0, seed=1)
+    E = np.array([-2.1, 0.3, 1.7])
+    sr, sl = W.self_energies(dev, len(E))
+    s = hsc.Solver(dev, 3)
+    dgr, dgl, _, _ = s.solve(E, ETA_WELL, sr, sl, precision=hsc.HSC_MIXED)
+    s.close()
+    Hd = dev.to_scipy().toarray()
+    for k in range(len(E)):
+        G, Gl = dense.solve(Hd, E[k], ETA_WELL, dev.contact_unknowns(), sr[k], sl[k])
+        assert relerr(dgr[k], np.diag(G)) <= 5e-3
+        assert relerr(dgl[k], np.diag(Gl)) <= 5e-3
