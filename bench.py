@@ -43,7 +43,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true")
-    p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E"],
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                   help="precision of the batch8 workload")
+    p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E", "batch8"],
                    help="cubic32: the metric workload; cubic24x8E: 24^3 grid, 8 energies (a few GB, "
                         "for ncu captures)")
     return p.parse_args()
@@ -332,10 +334,65 @@ def run_hsc(args):
     return 0
 
 
+def run_batch8(args):
+    """The batching workload: 256 energies linspace(-6, 6) dealt over 8 cuboids with uneven
+    separators (24^3 ... 48x24x40), all in one hsc_solve_batch CUDA-graph launch per step."""
+    import torch
+    from paper_1702_05167_gb300 import hsc, workloads as W
+    torch.cuda.set_device(0)
+    cfgs = W.batching()
+    items, solvers = [], []
+    for c in cfgs:
+        dev = c["dev"]
+        E = c["energies"]
+        sr, sl = W.self_energies(dev, len(E), c["f"])
+        s = hsc.Solver(dev, c["leaf"])
+        solvers.append(s)
+        n = dev.n
+        items.append(dict(h=s.h, E=torch.from_numpy(E).cuda(),
+                          sigma_r=torch.from_numpy(sr.view(np.float64)).cuda(),
+                          sigma_less=torch.from_numpy(sl.view(np.float64)).cuda(), pairs=None,
+                          diag_gr=torch.empty((len(E), 2 * n), dtype=torch.float64, device="cuda"),
+                          diag_gl=torch.empty((len(E), 2 * n), dtype=torch.float64, device="cuda")))
+    prec = hsc.HSC_FP64 if args.precision == "fp64" else hsc.HSC_MIXED
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        hsc.hsc_solve_batch(items, 1e-6, prec, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        hsc.hsc_solve_batch(items, 1e-6, prec, stream=stream.cuda_stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    nE = sum(len(c["energies"]) for c in cfgs)
+    flops = sum((s.stats.flops_gr + s.stats.flops_gl) * len(c["energies"]) for s, c in zip(solvers, cfgs))
+    line = {"metric": "energy pts/s, 8 cuboids x 32 energies in one CUDA-graph launch",
+            "value": nE * args.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "dtype": "c128" if prec == hsc.HSC_FP64 else "c128+tf32x3",
+            "data": "synthetic",
+            "config": {"workload": "batch8: " + ", ".join(c["name"] for c in cfgs),
+                       "energies": nE, "eta": 1e-6, "leaf_max": 8, "precision": args.precision,
+                       "launch": "hsc_solve_batch, one cached CUDA graph, one stream per cuboid"},
+            "model_tflops": flops * args.steps / (ms / 1000.0) / 1e12, "clocks": ck}
+    for s in solvers:
+        s.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch8":
+        return run_batch8(args)
     return run_hsc(args)
 
 

@@ -125,6 +125,68 @@ int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
               hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl,
               void* cuda_stream, int32_t io_on_device);
 
+/* Options of a handle (hsc_set_option / hsc_get_option). Setting one discards the handle's device
+ * schedule and workspace (rebuilt by the next solve). HSC_OPT_LEAF is read-only (the leaf_max of
+ * the last hsc_analyze). */
+typedef enum {
+  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 16)                   */
+  HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
+  HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
+  HSC_OPT_LEAF = 4            /* read only                                                      */
+} hsc_option;
+
+int hsc_set_option(hsc_t h, int32_t option, int32_t value);
+int hsc_get_option(hsc_t h, int32_t option, int32_t* value);
+
+/* One device of a batched solve (hsc_solve_batch). E, sigma_r, sigma_less and all outputs are device
+ * memory laid out as in hsc_solve; req_pairs is host memory. */
+typedef struct {
+  hsc_t h;
+  int64_t n_E;
+  const double* E;
+  const hsc_c128* sigma_r;
+  const hsc_c128* sigma_less;   /* may be NULL (no G^<)                                          */
+  int32_t n_req;
+  const int32_t* req_pairs;
+  hsc_c128* diag_gr;
+  hsc_c128* diag_gl;
+  hsc_c128* req_gr;
+  hsc_c128* req_gl;
+} hsc_batch_item;
+
+/* hsc_solve_batch -- solve several devices (handles, e.g. cuboids with uneven separators) and their
+ *   energies in one CUDA-graph launch. Each item's level schedule is captured on its own stream,
+ *   forked from and joined back into cuda_stream, so the items' kernels run concurrently and the
+ *   GPU balances the uneven trees (the capture runs on an internal stream; the graph is launched
+ *   into cuda_stream, which may be the legacy default stream). The instantiated graph is cached
+ *   and replayed while the items
+ *   (handles, pointers, sizes), eta and precision are unchanged. use_graph = 0 enqueues the same
+ *   work directly on the item streams (no graph). Workspaces are sized so that all items fit the
+ *   device budget together (energies of an item run in several waves if needed). The call
+ *   synchronises cuda_stream and checks every item's device error flags.
+ *   Errors: as hsc_solve; on error the item index is named in hsc_last_error(NULL). */
+int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, double eta, int32_t precision,
+                    void* cuda_stream, int32_t use_graph);
+
+/* Result of hsc_tune. */
+typedef struct {
+  int32_t leaf_max;        /* chosen nested-dissection leaf size                          */
+  int32_t gj_panel;        /* chosen Gauss-Jordan panel width                             */
+  double ms_per_energy;    /* measured time of the chosen configuration                   */
+  int32_t from_cache;      /* 1 if read from the cache file, 0 if measured now             */
+  int32_t n_tried;         /* configurations timed                                        */
+} hsc_tune_result;
+
+/* hsc_tune -- autotune a handle for its geometry on this GPU: for each candidate leaf_max (4, 6, 8,
+ *   when smaller than the grid) and Gauss-Jordan panel width (8, 16, 32) re-analyse, solve the given
+ *   probe energies twice (host buffers, as hsc_solve) and time the second solve with CUDA events;
+ *   keep the fastest, leave the handle analysed with it, and append one JSON line (GPU name, grid,
+ *   orbitals, precision, choice, time) to cache_path (may be NULL: no cache). A matching cache line
+ *   is applied without timing. Errors: as hsc_analyze / hsc_solve. */
+int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+             const hsc_c128* sigma_less, int32_t precision, const char* cache_path,
+             hsc_tune_result* out);
+
 /* Kernel-class statistics of the launches hsc_solve made since the last hsc_profile call.
  *   launches  kernel launches of the class (counted whether or not timing is enabled)
  *   timed     launches bracketed by CUDA events (only while timing is enabled)

@@ -104,6 +104,8 @@ extern "C" int hsc_create(hsc_t* out, int64_t n, int32_t orb, const int64_t* row
 extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
   h->analyzed = false;
+  hsc::device_state_free(h->dev);   // the device schedule belongs to the previous tree
+  h->dev = nullptr;
   hsc::Input in;
   in.n = h->n;
   in.orb = h->orb;
@@ -137,6 +139,7 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   s.bytes_per_energy = (4 * P.tot_aug + 2 * P.tot_sq) * 16;
   h->stats = s;
   if (stats) *stats = s;
+  h->leaf_max = leaf_max;
   h->analyzed = true;
   h->err.clear();
   return HSC_OK;
@@ -165,6 +168,40 @@ extern "C" int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* 
   if (upd)
     for (size_t k = 0; k < c.usites.size(); ++k)
       for (int o = 0; o < orb; ++o) upd[k * orb + o] = c.usites[k] * orb + o;
+  return HSC_OK;
+}
+
+extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  switch (option) {
+    case HSC_OPT_GJ_PANEL:
+      if (value < 1 || value > 64) return hsc_fail(h, HSC_ERR_ARG, "panel width must be in [1, 64]");
+      h->opt_nb = value;
+      break;
+    case HSC_OPT_FP64_LEVELS:
+      if (value < 0) return hsc_fail(h, HSC_ERR_ARG, "levels must be >= 0");
+      h->opt_fp64_levels = value;
+      break;
+    case HSC_OPT_MIXED_GJ_FP64:
+      h->opt_gj_fp64 = value != 0;
+      break;
+    default:
+      return hsc_fail(h, HSC_ERR_ARG, "unknown option");
+  }
+  hsc::device_state_free(h->dev);   // schedules depend on the options
+  h->dev = nullptr;
+  return HSC_OK;
+}
+
+extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
+  if (!h || !value) return hsc_fail(h, HSC_ERR_ARG, "NULL argument");
+  switch (option) {
+    case HSC_OPT_GJ_PANEL: *value = h->opt_nb; break;
+    case HSC_OPT_FP64_LEVELS: *value = h->opt_fp64_levels; break;
+    case HSC_OPT_MIXED_GJ_FP64: *value = h->opt_gj_fp64; break;
+    case HSC_OPT_LEAF: *value = h->leaf_max; break;
+    default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
+  }
   return HSC_OK;
 }
 

@@ -27,6 +27,11 @@ struct hsc_ctx {
   hsc_tree_stats stats{};
   std::string err;
   hsc::DeviceState* dev = nullptr;
+  // options (hsc_set_option); they survive re-analysis
+  int opt_nb = 16;            // Gauss-Jordan panel width
+  int opt_fp64_levels = 2;    // HSC_MIXED: top tree levels kept on the FP64 pipe
+  int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe
+  int leaf_max = 0;           // last hsc_analyze leaf size
 };
 
 int hsc_fail(hsc_ctx* h, int code, const std::string& msg);

@@ -65,8 +65,11 @@ struct Prof {
   int64_t launches[K_NCLASS] = {0};
 };
 
+static uint64_t g_generation = 0;   // distinguishes device states across re-creation
+
 struct DeviceState {
   int device = -1;
+  uint64_t gen = ++g_generation;
   Prof prof;
   bool planned = false;
   int nb = 16;                       // Gauss-Jordan panel width
@@ -94,9 +97,12 @@ struct DeviceState {
       *X = nullptr, *T = nullptr, *Z = nullptr, *GUU = nullptr, *PUU = nullptr, *N = nullptr,
       *GJT = nullptr;
   int32_t* piv = nullptr;
-  // host-io staging
-  int64_t io_cap = 0, io_n = 0, io_ncs = 0, io_req = 0;
+  // host-io staging, requested-pair offsets, batch branch stream
+  int64_t io_cap = 0;
   void* io = nullptr;
+  int64_t* poff = nullptr;
+  int64_t pair_cap = 0;
+  cudaStream_t branch = nullptr;
   std::vector<void*> fixed;          // energy-independent allocations
 };
 
@@ -109,6 +115,8 @@ void device_state_free(DeviceState* d) {
   for (cudaEvent_t e : d->prof.pool) cudaEventDestroy(e);
   if (d->arena) cudaFree(d->arena);
   if (d->io) cudaFree(d->io);
+  if (d->poff) cudaFree(d->poff);
+  if (d->branch) cudaStreamDestroy(d->branch);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
 }
@@ -647,39 +655,21 @@ int64_t budget_bytes() {
 
 using namespace hsc;
 
-extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
-                         const hsc_c128* sigma_less, int32_t precision, int32_t n_req,
-                         const int32_t* req_pairs, hsc_c128* diag_gr, hsc_c128* diag_gl,
-                         hsc_c128* req_gr, hsc_c128* req_gl, void* cuda_stream, int32_t io_on_device) {
-  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
-  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
-  if (n_E < 0 || (!E && n_E > 0)) return hsc_fail(h, HSC_ERR_ARG, "bad energy array");
-  if (n_E == 0) return HSC_OK;
-  if (!diag_gr) return hsc_fail(h, HSC_ERR_ARG, "diag_gr is NULL");
-  if (sigma_less && !diag_gl) return hsc_fail(h, HSC_ERR_ARG, "diag_gl is NULL");
-  if (h->n_contact_unknowns > 0 && !sigma_r) return hsc_fail(h, HSC_ERR_ARG, "sigma_r is NULL");
-  if (n_req < 0 || (n_req > 0 && (!req_pairs || !req_gr || (sigma_less && !req_gl))))
-    return hsc_fail(h, HSC_ERR_ARG, "bad requested-pair arrays");
-  if (precision != HSC_FP64 && precision != HSC_MIXED)
-    return hsc_fail(h, HSC_ERR_ARG, "precision must be HSC_FP64 or HSC_MIXED");
-  if (!(eta >= 0.0)) return hsc_fail(h, HSC_ERR_ARG, "eta must be >= 0");
-  const Plan& P = h->plan;
-  std::vector<int64_t> poff(n_req);
-  for (int k = 0; k < n_req; ++k) {
-    int64_t a = req_pairs[2 * k], b = req_pairs[2 * k + 1];
-    if (a < 0 || a >= h->n || b < 0 || b >= h->n) return hsc_fail(h, HSC_ERR_ARG, "pair index out of range");
-    if (!locate_pair(P, a, b, &poff[k]))
-      return hsc_fail(h, HSC_ERR_NOT_SELECTED, "pair (" + std::to_string(a) + "," + std::to_string(b) +
-                                                   ") is outside the filled pattern");
-  }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
+namespace hsc {
+namespace {
+
+// Creates the device state (applying the handle's options) and the device schedule.
+int get_state(hsc_ctx* h) {
   if (!h->dev) {
     h->dev = new DeviceState();
     CK(cudaGetDevice(&h->dev->device));
+    h->dev->nb = h->opt_nb;
+    h->dev->fp64_levels = h->opt_fp64_levels;
+    h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
+    if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
+    if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
   }
   DeviceState* d = h->dev;
-  if (const char* v = getenv("HSC_FP64_LEVELS")) d->fp64_levels = atoi(v);
-  if (const char* v = getenv("HSC_MIXED_GJ_FP64")) d->gj_fp64 = atoi(v) != 0;
   int cur = 0;
   CK(cudaGetDevice(&cur));
   if (cur != d->device) return hsc_fail(h, HSC_ERR_ARG, "current device differs from the handle's device");
@@ -692,25 +682,120 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     }
     if (rc != HSC_OK) return rc;
   }
+  return HSC_OK;
+}
+
+int check_common(hsc_ctx* h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                 const hsc_c128* sigma_less, int32_t precision, int32_t n_req,
+                 const int32_t* req_pairs, const hsc_c128* diag_gr, const hsc_c128* diag_gl,
+                 const hsc_c128* req_gr, const hsc_c128* req_gl) {
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  if (n_E < 0 || (!E && n_E > 0)) return hsc_fail(h, HSC_ERR_ARG, "bad energy array");
+  if (n_E > 0 && !diag_gr) return hsc_fail(h, HSC_ERR_ARG, "diag_gr is NULL");
+  if (sigma_less && !diag_gl) return hsc_fail(h, HSC_ERR_ARG, "diag_gl is NULL");
+  if (h->n_contact_unknowns > 0 && !sigma_r) return hsc_fail(h, HSC_ERR_ARG, "sigma_r is NULL");
+  if (n_req < 0 || (n_req > 0 && (!req_pairs || !req_gr || (sigma_less && !req_gl))))
+    return hsc_fail(h, HSC_ERR_ARG, "bad requested-pair arrays");
+  if (precision != HSC_FP64 && precision != HSC_MIXED)
+    return hsc_fail(h, HSC_ERR_ARG, "precision must be HSC_FP64 or HSC_MIXED");
+  if (!(eta >= 0.0)) return hsc_fail(h, HSC_ERR_ARG, "eta must be >= 0");
+  return HSC_OK;
+}
+
+// Locates the requested pairs and copies their source offsets into a persistent device buffer.
+int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
+  DeviceState* d = h->dev;
+  std::vector<int64_t> poff(n_req);
+  for (int k = 0; k < n_req; ++k) {
+    int64_t a = req_pairs[2 * k], b = req_pairs[2 * k + 1];
+    if (a < 0 || a >= h->n || b < 0 || b >= h->n) return hsc_fail(h, HSC_ERR_ARG, "pair index out of range");
+    if (!locate_pair(h->plan, a, b, &poff[k]))
+      return hsc_fail(h, HSC_ERR_NOT_SELECTED, "pair (" + std::to_string(a) + "," + std::to_string(b) +
+                                                   ") is outside the filled pattern");
+  }
+  if (n_req > d->pair_cap) {
+    if (d->poff) cudaFree(d->poff);
+    d->poff = nullptr;
+    d->pair_cap = 0;
+    if (cudaMalloc((void**)&d->poff, (size_t)n_req * sizeof(int64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc pair offsets");
+    }
+    d->pair_cap = n_req;
+  }
+  if (n_req > 0) CK(cudaMemcpy(d->poff, poff.data(), n_req * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return HSC_OK;
+}
+
+// Sizes (and allocates) the workspace for waves of at most `wave` energies.
+int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out) {
+  DeviceState* d = h->dev;
   const int64_t per = bytes_per_energy(d);
-  int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(budget_bytes() / per, 0));
+  int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(byte_cap / per, 0));
   if (d->cap > 0) wave = std::max<int64_t>(std::min<int64_t>(n_E, d->cap), wave);
   if (wave <= 0) return hsc_fail(h, HSC_ERR_OOM, "one energy needs " + std::to_string(per >> 20) + " MiB of workspace");
   wave = std::min<int64_t>(wave, 65535);
   int rc = ensure_arena(h, wave);
   if (rc != HSC_OK) return rc;
+  *wave_out = wave;
+  return HSC_OK;
+}
 
+// Enqueues all waves of a device-resident solve on stream s (no host synchronisation).
+int enqueue_device(hsc_ctx* h, int64_t n_E, int64_t wave, const double* E, double eta,
+                   const hsc_c128* sigma_r, const hsc_c128* sigma_less, int32_t precision,
+                   int32_t n_req, hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr,
+                   hsc_c128* req_gl, cudaStream_t s) {
+  DeviceState* d = h->dev;
   const int64_t n = h->n, ncs = h->n_contact_unknowns;
-  int64_t* d_poff = nullptr;
-  if (n_req > 0) {
-    CK(cudaMallocAsync((void**)&d_poff, n_req * sizeof(int64_t), s));
-    CK(cudaMemcpyAsync(d_poff, poff.data(), n_req * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  }
   CK(cudaMemsetAsync(d->flag, 0, 4 * sizeof(int), s));
-  // host io: staging buffers for one wave
-  double* sE = nullptr;
-  c64 *ssr = nullptr, *ssl = nullptr, *sgr = nullptr, *sgl = nullptr, *spr = nullptr, *spl = nullptr;
-  if (!io_on_device) {
+  for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
+    const int ne = (int)std::min<int64_t>(wave, n_E - e0);
+    const c64* dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
+    const c64* dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
+    c64* ogr = reinterpret_cast<c64*>(diag_gr) + e0 * n;
+    c64* ogl = diag_gl ? reinterpret_cast<c64*>(diag_gl) + e0 * n : nullptr;
+    c64* pgr = req_gr ? reinterpret_cast<c64*>(req_gr) + e0 * n_req : nullptr;
+    c64* pgl = req_gl ? reinterpret_cast<c64*>(req_gl) + e0 * n_req : nullptr;
+    int rc = run_wave(h, ne, E + e0, eta, dsr, dsl, n_req, d->poff, ogr, ogl, pgr, pgl, precision, s);
+    if (rc != HSC_OK) return rc;
+  }
+  return HSC_OK;
+}
+
+int read_flags(hsc_ctx* h, cudaStream_t s) {
+  int flags[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(flags, h->dev->flag, sizeof(flags), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags[1]) return hsc_fail(h, HSC_ERR_ARG, "internal gather map error");
+  if (flags[2]) return hsc_fail(h, HSC_ERR_TIMEOUT, "a tensor-core GEMM wait expired");
+  if (flags[0]) return hsc_fail(h, HSC_ERR_SINGULAR, "zero pivot in a cluster block");
+  return HSC_OK;
+}
+
+}  // namespace
+}  // namespace hsc
+
+extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                         const hsc_c128* sigma_less, int32_t precision, int32_t n_req,
+                         const int32_t* req_pairs, hsc_c128* diag_gr, hsc_c128* diag_gl,
+                         hsc_c128* req_gr, hsc_c128* req_gl, void* cuda_stream, int32_t io_on_device) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  int rc = check_common(h, n_E, E, eta, sigma_r, sigma_less, precision, n_req, req_pairs, diag_gr,
+                        diag_gl, req_gr, req_gl);
+  if (rc != HSC_OK || n_E == 0) return rc;
+  if ((rc = get_state(h)) != HSC_OK) return rc;
+  if ((rc = upload_pairs(h, n_req, req_pairs)) != HSC_OK) return rc;
+  DeviceState* d = h->dev;
+  int64_t wave = 0;
+  if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave)) != HSC_OK) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (io_on_device) {
+    rc = enqueue_device(h, n_E, wave, E, eta, sigma_r, sigma_less, precision, n_req, diag_gr, diag_gl,
+                        req_gr, req_gl, s);
+    if (rc != HSC_OK) return rc;
+  } else {
+    const int64_t n = h->n, ncs = h->n_contact_unknowns;
     int64_t need = wave * (int64_t)(8 + 16 * (2 * ncs + 2 * n + 2 * (int64_t)n_req)) + 8 * 256;
     if (d->io_cap < need) {
       if (d->io) cudaFree(d->io);
@@ -722,39 +807,24 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     }
     char* p = (char*)d->io;
     auto take = [&](int64_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
-    sE = (double*)take(wave * 8);
-    ssr = (c64*)take(wave * ncs * 16);
-    ssl = (c64*)take(wave * ncs * 16);
-    sgr = (c64*)take(wave * n * 16);
-    sgl = (c64*)take(wave * n * 16);
-    spr = (c64*)take(wave * (int64_t)n_req * 16);
-    spl = (c64*)take(wave * (int64_t)n_req * 16);
-  }
-  for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
-    const int ne = (int)std::min<int64_t>(wave, n_E - e0);
-    const double* dE;
-    const c64 *dsr, *dsl;
-    c64 *ogr, *ogl, *pgr, *pgl;
-    if (io_on_device) {
-      dE = E + e0;
-      dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
-      dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
-      ogr = reinterpret_cast<c64*>(diag_gr) + e0 * n;
-      ogl = diag_gl ? reinterpret_cast<c64*>(diag_gl) + e0 * n : nullptr;
-      pgr = req_gr ? reinterpret_cast<c64*>(req_gr) + e0 * n_req : nullptr;
-      pgl = req_gl ? reinterpret_cast<c64*>(req_gl) + e0 * n_req : nullptr;
-    } else {
+    double* sE = (double*)take(wave * 8);
+    c64* ssr = (c64*)take(wave * ncs * 16);
+    c64* ssl = (c64*)take(wave * ncs * 16);
+    c64* sgr = (c64*)take(wave * n * 16);
+    c64* sgl = (c64*)take(wave * n * 16);
+    c64* spr = (c64*)take(wave * (int64_t)n_req * 16);
+    c64* spl = (c64*)take(wave * (int64_t)n_req * 16);
+    CK(cudaMemsetAsync(d->flag, 0, 4 * sizeof(int), s));
+    for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
+      const int ne = (int)std::min<int64_t>(wave, n_E - e0);
       CK(cudaMemcpyAsync(sE, E + e0, ne * 8, cudaMemcpyHostToDevice, s));
       if (ncs > 0) {
         CK(cudaMemcpyAsync(ssr, sigma_r + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
         if (sigma_less) CK(cudaMemcpyAsync(ssl, sigma_less + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
       }
-      dE = sE; dsr = ssr; dsl = sigma_less ? ssl : nullptr;
-      ogr = sgr; ogl = sgl; pgr = spr; pgl = spl;
-    }
-    rc = run_wave(h, ne, dE, eta, dsr, dsl, n_req, d_poff, ogr, ogl, pgr, pgl, precision, s);
-    if (rc != HSC_OK) return rc;
-    if (!io_on_device) {
+      rc = run_wave(h, ne, sE, eta, ssr, sigma_less ? ssl : nullptr, n_req, d->poff, sgr, sgl, spr,
+                    spl, precision, s);
+      if (rc != HSC_OK) return rc;
       CK(cudaMemcpyAsync(diag_gr + e0 * n, sgr, ne * n * 16, cudaMemcpyDeviceToHost, s));
       if (sigma_less) CK(cudaMemcpyAsync(diag_gl + e0 * n, sgl, ne * n * 16, cudaMemcpyDeviceToHost, s));
       if (n_req > 0) {
@@ -763,13 +833,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
       }
     }
   }
-  if (d_poff) CK(cudaFreeAsync(d_poff, s));
-  int flags[4] = {0, 0, 0, 0};
-  CK(cudaMemcpyAsync(flags, d->flag, sizeof(flags), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (flags[1]) return hsc_fail(h, HSC_ERR_ARG, "internal gather map error");
-  if (flags[2]) return hsc_fail(h, HSC_ERR_TIMEOUT, "a tensor-core GEMM wait expired");
-  if (flags[0]) return hsc_fail(h, HSC_ERR_SINGULAR, "zero pivot in a cluster block");
+  if ((rc = read_flags(h, s)) != HSC_OK) return rc;
   h->err.clear();
   return HSC_OK;
 }
@@ -884,5 +948,249 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   cudaFree(flag);
   if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, cudaGetErrorString(e));
   if (hf) return hsc_fail(nullptr, HSC_ERR_TIMEOUT, "tensor-core GEMM wait expired");
+  return HSC_OK;
+}
+
+// ---- batched solve in one CUDA graph -----------------------------------------------------------
+
+namespace hsc {
+namespace {
+
+struct GraphCache {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;     // capture stream (the legacy default stream cannot be captured)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+};
+GraphCache g_graph;
+
+uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
+
+}  // namespace
+}  // namespace hsc
+
+extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, double eta,
+                               int32_t precision, void* cuda_stream, int32_t use_graph) {
+  if (n_items <= 0 || !items) return hsc_fail(nullptr, HSC_ERR_ARG, "no batch items");
+  auto item_fail = [&](int i, hsc_ctx* h, int rc) {
+    return hsc_fail(nullptr, rc, "batch item " + std::to_string(i) + ": " + (h ? h->err : std::string("")));
+  };
+  double need_total = 0;
+  std::vector<double> need(n_items, 0.0);
+  for (int i = 0; i < n_items; ++i) {
+    const hsc_batch_item& it = items[i];
+    hsc_ctx* h = it.h;
+    if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "batch item " + std::to_string(i) + ": NULL handle");
+    for (int j = 0; j < i; ++j)
+      if (items[j].h == h) return hsc_fail(nullptr, HSC_ERR_ARG, "a handle appears twice in the batch");
+    int rc = check_common(h, it.n_E, it.E, eta, it.sigma_r, it.sigma_less, precision, it.n_req,
+                          it.req_pairs, it.diag_gr, it.diag_gl, it.req_gr, it.req_gl);
+    if (rc == HSC_OK) rc = get_state(h);
+    if (rc == HSC_OK) rc = upload_pairs(h, it.n_req, it.req_pairs);
+    if (rc != HSC_OK) return item_fail(i, h, rc);
+    need[i] = (double)bytes_per_energy(h->dev) * (double)std::max<int64_t>(it.n_E, 1);
+    need_total += need[i];
+  }
+  const double budget = (double)budget_bytes();
+  std::vector<int64_t> wave(n_items, 0);
+  for (int i = 0; i < n_items; ++i) {
+    hsc_ctx* h = items[i].h;
+    int64_t cap = (int64_t)(budget * need[i] / need_total);
+    int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i]);
+    if (rc != HSC_OK) return item_fail(i, h, rc);
+    if (!h->dev->branch) {
+      cudaError_t e = cudaStreamCreateWithFlags(&h->dev->branch, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, "cudaStreamCreate");
+    }
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<uint64_t> key = {(uint64_t)n_items, (uint64_t)precision};
+  {
+    uint64_t eb;
+    std::memcpy(&eb, &eta, sizeof(eb));
+    key.push_back(eb);
+    key.push_back(u64(s));
+  }
+  for (int i = 0; i < n_items; ++i) {
+    const hsc_batch_item& it = items[i];
+    DeviceState* d = it.h->dev;
+    for (uint64_t v : {u64(it.h), d->gen, u64(d->arena), (uint64_t)d->cap, (uint64_t)it.n_E, u64(it.E),
+                       u64(it.sigma_r), u64(it.sigma_less), (uint64_t)it.n_req, u64(d->poff),
+                       u64(it.diag_gr), u64(it.diag_gl), u64(it.req_gr), u64(it.req_gl),
+                       (uint64_t)wave[i]})
+      key.push_back(v);
+  }
+  auto enqueue_all = [&](cudaStream_t s) -> int {
+    for (int i = 0; i < n_items; ++i) {
+      const hsc_batch_item& it = items[i];
+      hsc_ctx* h = it.h;
+      cudaStream_t b = h->dev->branch;
+      if (cudaStreamWaitEvent(b, g_graph.fork, 0) != cudaSuccess)
+        return hsc_fail(nullptr, HSC_ERR_CUDA, "cudaStreamWaitEvent");
+      if (it.n_E > 0) {
+        const bool prof = h->dev->prof.on;
+        if (use_graph) h->dev->prof.on = false;   // no event bookkeeping inside a captured graph
+        int rc = enqueue_device(h, it.n_E, wave[i], it.E, eta, it.sigma_r, it.sigma_less, precision,
+                                it.n_req, it.diag_gr, it.diag_gl, it.req_gr, it.req_gl, b);
+        h->dev->prof.on = prof;
+        if (rc != HSC_OK) return item_fail(i, h, rc);
+      }
+      if (cudaEventRecord(g_graph.join[i], b) != cudaSuccess ||
+          cudaStreamWaitEvent(s, g_graph.join[i], 0) != cudaSuccess)
+        return hsc_fail(nullptr, HSC_ERR_CUDA, "join events");
+    }
+    return HSC_OK;
+  };
+  if (!g_graph.fork && cudaEventCreateWithFlags(&g_graph.fork, cudaEventDisableTiming) != cudaSuccess)
+    return hsc_fail(nullptr, HSC_ERR_CUDA, "cudaEventCreate");
+  while ((int)g_graph.join.size() < n_items) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return hsc_fail(nullptr, HSC_ERR_CUDA, "cudaEventCreate");
+    g_graph.join.push_back(e);
+  }
+  if (use_graph) {
+    if (!(g_graph.exec && g_graph.key == key)) {
+      if (g_graph.exec) cudaGraphExecDestroy(g_graph.exec);
+      g_graph.exec = nullptr;
+      g_graph.key.clear();
+      if (!g_graph.cap && cudaStreamCreateWithFlags(&g_graph.cap, cudaStreamNonBlocking) != cudaSuccess)
+        return hsc_fail(nullptr, HSC_ERR_CUDA, "cudaStreamCreate");
+      cudaStream_t cs = g_graph.cap;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      int rc = HSC_OK;
+      if (cudaEventRecord(g_graph.fork, cs) != cudaSuccess) rc = hsc_fail(nullptr, HSC_ERR_CUDA, "fork event");
+      if (rc == HSC_OK) rc = enqueue_all(cs);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      if (rc != HSC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&g_graph.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g_graph.exec = nullptr;
+        return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      g_graph.key = key;
+    }
+    cudaError_t e = cudaGraphLaunch(g_graph.exec, s);
+    if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  } else {
+    if (cudaEventRecord(g_graph.fork, s) != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, "fork event");
+    int rc = enqueue_all(s);
+    if (rc != HSC_OK) return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < n_items; ++i) {
+    int rc = read_flags(items[i].h, s);
+    if (rc != HSC_OK) return item_fail(i, items[i].h, rc);
+  }
+  return HSC_OK;
+}
+
+// ---- autotuner -----------------------------------------------------------------------------------
+
+extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                        const hsc_c128* sigma_less, int32_t precision, const char* cache_path,
+                        hsc_tune_result* out) {
+  if (!h || !out || n_E <= 0 || !E) return hsc_fail(h, HSC_ERR_ARG, "bad tune arguments");
+  cudaDeviceProp prop;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return hsc_fail(h, HSC_ERR_CUDA, "no CUDA device");
+  char keybuf[512];
+  std::snprintf(keybuf, sizeof(keybuf), "\"gpu\": \"%s\", \"dims\": [%d, %d, %d], \"orb\": %d, \"n\": %lld, \"precision\": %d",
+                prop.name, h->dims[0], h->dims[1], h->dims[2], h->orb, (long long)h->n, precision);
+  const std::string key(keybuf);
+  std::memset(out, 0, sizeof(*out));
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[1024];
+      int leaf = -1, nb = -1;
+      double ms = 0;
+      while (std::fgets(line, sizeof(line), f)) {
+        if (!std::strstr(line, key.c_str())) continue;
+        const char* a = std::strstr(line, "\"leaf_max\": ");
+        const char* b = std::strstr(line, "\"gj_panel\": ");
+        const char* c = std::strstr(line, "\"ms_per_energy\": ");
+        if (a && b) {
+          leaf = std::atoi(a + 12);
+          nb = std::atoi(b + 12);
+          ms = c ? std::atof(c + 17) : 0;
+        }
+      }
+      std::fclose(f);
+      if (leaf > 0 && nb > 0) {
+        int rc = hsc_analyze(h, leaf, nullptr);
+        if (rc == HSC_OK) rc = hsc_set_option(h, HSC_OPT_GJ_PANEL, nb);
+        if (rc != HSC_OK) return rc;
+        out->leaf_max = leaf;
+        out->gj_panel = nb;
+        out->ms_per_energy = ms;
+        out->from_cache = 1;
+        return HSC_OK;
+      }
+    }
+  }
+  const int64_t n = h->n;
+  const int64_t ncs = h->n_contact_unknowns;
+  std::vector<hsc_c128> gr(n_E * n), gl(sigma_less ? n_E * n : 0);
+  int maxdim = std::max(h->dims[0], std::max(h->dims[1], h->dims[2]));
+  if (maxdim <= 0) maxdim = 1 << 30;
+  std::vector<int> leaves;
+  for (int l : {4, 6, 8})
+    if (l < maxdim) leaves.push_back(l);
+  if (leaves.empty()) leaves.push_back(h->leaf_max > 0 ? h->leaf_max : 4);
+  double best = 1e300;
+  int best_leaf = leaves[0], best_nb = 16, tried = 0;
+  (void)ncs;
+  for (int leaf : leaves)
+    for (int nb : {8, 16, 32}) {
+      int rc = hsc_analyze(h, leaf, nullptr);
+      if (rc == HSC_OK) rc = hsc_set_option(h, HSC_OPT_GJ_PANEL, nb);
+      if (rc == HSC_OK)
+        rc = hsc_solve(h, n_E, E, eta, sigma_r, sigma_less, precision, 0, nullptr, gr.data(),
+                       sigma_less ? gl.data() : nullptr, nullptr, nullptr, nullptr, 0);
+      if (rc != HSC_OK) return rc;
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, 0);
+      rc = hsc_solve(h, n_E, E, eta, sigma_r, sigma_less, precision, 0, nullptr, gr.data(),
+                     sigma_less ? gl.data() : nullptr, nullptr, nullptr, nullptr, 0);
+      cudaEventRecord(b, 0);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      if (rc != HSC_OK) return rc;
+      ++tried;
+      if (ms < best) {
+        best = ms;
+        best_leaf = leaf;
+        best_nb = nb;
+      }
+    }
+  int rc = hsc_analyze(h, best_leaf, nullptr);
+  if (rc == HSC_OK) rc = hsc_set_option(h, HSC_OPT_GJ_PANEL, best_nb);
+  if (rc != HSC_OK) return rc;
+  out->leaf_max = best_leaf;
+  out->gj_panel = best_nb;
+  out->ms_per_energy = best / (double)n_E;
+  out->n_tried = tried;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "{%s, \"leaf_max\": %d, \"gj_panel\": %d, \"ms_per_energy\": %.6f}\n", key.c_str(),
+                   best_leaf, best_nb, out->ms_per_energy);
+      std::fclose(f);
+    }
+  }
   return HSC_OK;
 }

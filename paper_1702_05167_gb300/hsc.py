@@ -17,8 +17,10 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
           4: "HSC_ERR_SINGULAR", 5: "HSC_ERR_NOT_SELECTED", 6: "HSC_ERR_OOM", 7: "HSC_ERR_CUDA",
           8: "HSC_ERR_TIMEOUT"}
 
-EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_profile",
-           "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_last_error", "hsc_destroy"]
+EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
+           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read",
+           "hsc_device_fp64_peaks", "hsc_last_error", "hsc_destroy"]
+HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF = 1, 2, 3, 4
 
 
 class hsc_tree_stats(ctypes.Structure):
@@ -38,6 +40,20 @@ class hsc_cluster_info(ctypes.Structure):
 class hsc_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("timed", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class hsc_batch_item(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("n_E", ctypes.c_int64), ("E", ctypes.c_void_p),
+                ("sigma_r", ctypes.c_void_p), ("sigma_less", ctypes.c_void_p),
+                ("n_req", ctypes.c_int32), ("req_pairs", ctypes.c_void_p),
+                ("diag_gr", ctypes.c_void_p), ("diag_gl", ctypes.c_void_p),
+                ("req_gr", ctypes.c_void_p), ("req_gl", ctypes.c_void_p)]
+
+
+class hsc_tune_result(ctypes.Structure):
+    _fields_ = [("leaf_max", ctypes.c_int32), ("gj_panel", ctypes.c_int32),
+                ("ms_per_energy", ctypes.c_double), ("from_cache", ctypes.c_int32),
+                ("n_tried", ctypes.c_int32)]
 
 
 class HSCError(RuntimeError):
@@ -68,13 +84,19 @@ def load():
     L.hsc_analyze.argtypes = [vp, i32, ctypes.POINTER(hsc_tree_stats)]
     L.hsc_cluster.argtypes = [vp, i32, ctypes.POINTER(hsc_cluster_info), vp, vp]
     L.hsc_solve.argtypes = [vp, i64, vp, dp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, i32]
+    L.hsc_solve_batch.argtypes = [i32, ctypes.POINTER(hsc_batch_item), dp, i32, vp, i32]
+    L.hsc_tune.argtypes = [vp, i64, vp, dp, vp, vp, i32, ctypes.c_char_p,
+                           ctypes.POINTER(hsc_tune_result)]
+    L.hsc_set_option.argtypes = [vp, i32, i32]
+    L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
     L.hsc_profile.argtypes = [vp, i32]
     L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(hsc_kernel_stat), i32, ctypes.POINTER(i32)]
     L.hsc_device_fp64_peaks.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
     L.hsc_last_error.argtypes = [vp]
     L.hsc_last_error.restype = ctypes.c_char_p
     L.hsc_destroy.argtypes = [vp]
-    for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_profile",
+    for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
+                 "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile",
                  "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
@@ -149,6 +171,50 @@ def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, dia
                             int(precision), n_req, _ptr(pairs), _ptr(diag_gr), _ptr(diag_gl),
                             _ptr(req_gr), _ptr(req_gl), s, 1 if io_on_device else 0)
     _check(h, code)
+
+
+def hsc_set_option(h, option, value):
+    _check(h, load().hsc_set_option(h, int(option), int(value)))
+
+
+def hsc_get_option(h, option):
+    v = ctypes.c_int32()
+    _check(h, load().hsc_get_option(h, int(option), ctypes.byref(v)))
+    return v.value
+
+
+def hsc_solve_batch(items, eta, precision, stream=None, use_graph=True):
+    """items: list of dicts with keys h, E, sigma_r, sigma_less, pairs, diag_gr, diag_gl, req_gr,
+    req_gl (device tensors except `pairs`, a host int32 array or None)."""
+    arr = (hsc_batch_item * len(items))()
+    keep = []
+    for k, it in enumerate(items):
+        pairs = it.get("pairs")
+        if pairs is not None and len(pairs):
+            pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+            keep.append(pairs)
+        else:
+            pairs = None
+        arr[k] = hsc_batch_item(it["h"], int(it["E"].shape[0]), _ptr(it["E"]), _ptr(it["sigma_r"]),
+                                _ptr(it.get("sigma_less")), 0 if pairs is None else len(pairs),
+                                _ptr(pairs), _ptr(it["diag_gr"]), _ptr(it.get("diag_gl")),
+                                _ptr(it.get("req_gr")), _ptr(it.get("req_gl")))
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(None, load().hsc_solve_batch(len(items), arr, float(eta), int(precision), s,
+                                        1 if use_graph else 0))
+
+
+def hsc_tune(h, E, eta, sigma_r, sigma_less, precision=HSC_FP64, cache_path=None):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    sigma_r = np.ascontiguousarray(sigma_r, dtype=np.complex128)
+    if sigma_less is not None:
+        sigma_less = np.ascontiguousarray(sigma_less, dtype=np.complex128)
+    r = hsc_tune_result()
+    cp = None if cache_path is None else str(cache_path).encode()
+    _check(h, load().hsc_tune(h, len(E), _ptr(E), float(eta), _ptr(sigma_r), _ptr(sigma_less),
+                              int(precision), cp, ctypes.byref(r)))
+    return dict(leaf_max=r.leaf_max, gj_panel=r.gj_panel, ms_per_energy=r.ms_per_energy,
+                from_cache=bool(r.from_cache), n_tried=r.n_tried)
 
 
 def hsc_profile(h, enable):

@@ -145,3 +145,20 @@ def test_degenerate_chain_tree():
     most two entries (the separator structure that makes HSC coincide with RGF, Section 2.2)."""
     st, cl = _tree(W.chain_device(31), 1)
     assert st.max_n == 1 and st.max_m <= 2
+
+
+def test_options_round_trip_and_reject_bad_values():
+    dev = W.cubic_device((4, 4, 4), seed=0)
+    h = _handle(dev)
+    hsc.hsc_analyze(h, 2)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 16
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF) == 2
+    hsc.hsc_set_option(h, hsc.HSC_OPT_GJ_PANEL, 8)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 8
+    for opt, val in ((hsc.HSC_OPT_GJ_PANEL, 0), (hsc.HSC_OPT_GJ_PANEL, 65), (99, 1)):
+        with pytest.raises(hsc.HSCError) as ei:
+            hsc.hsc_set_option(h, opt, val)
+        assert ei.value.code == hsc.HSC_ERR_ARG
+    with pytest.raises(hsc.HSCError):
+        hsc.hsc_solve_batch([], 0.05, hsc.HSC_FP64)
+    hsc.hsc_destroy(h)
