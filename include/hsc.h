@@ -211,6 +211,18 @@ int hsc_profile(hsc_t h, int32_t enable);
  *   out = NULL to query *n_out). Waits for the recorded events. Errors: HSC_ERR_ARG, HSC_ERR_CUDA. */
 int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int32_t* n_out);
 
+/* hsc_observables -- per-energy observables from hsc_solve outputs (Section 1: the quantities the
+ *   Green's functions are evaluated for), all arrays on the device:
+ *   out[n_E][3] = { DOS(E) = -(1/pi) sum_u Im G^r_uu,
+ *                   T(E) = sum over the slots of `contact` of Gamma_slot Im G^<_uu with
+ *                          Gamma_slot = -2 Im Sigma^r_slot (the transmission into that contact when
+ *                          only the other contact is filled, f = 1),
+ *                   sum_u Im G^<_uu (2 pi times the electron count per unit energy) }.
+ *   diag_gl and sigma_r may be NULL (then the last two entries are 0). Asynchronous on cuda_stream.
+ *   Errors: HSC_ERR_ARG, HSC_ERR_STATE, HSC_ERR_CUDA. */
+int hsc_observables(hsc_t h, int64_t n_E, const hsc_c128* diag_gr, const hsc_c128* diag_gl,
+                    const hsc_c128* sigma_r, int32_t contact, double* out, void* cuda_stream);
+
 /* hsc_device_fp64_peaks -- measure, on the current device, the throughput of the FP64 tensor pipe
  *   (mma.sync m8n8k4 f64, which the complex128 GEMMs use) and of scalar FP64 FMA, in GFLOP/s
  *   (best of three ~10 ms launches). These are the roofline denominators of the complex128 path.

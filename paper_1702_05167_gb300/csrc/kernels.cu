@@ -339,7 +339,46 @@ __global__ void k_out_pairs(const int64_t* poff, int64_t npair, const c64* G, co
   }
 }
 
+// ---- observables: DOS = -(1/pi) sum_u Im G^r_uu, lesser trace = sum_u Im G^<_uu,
+//      T = sum over the slots of one contact of Gamma_slot Im G^<_(slot unknown), Gamma = -2 Im Sigma^r
+__global__ void k_observables(int64_t n, const c64* gr, const c64* gl, const c64* sr, int64_t ncs,
+                              const int64_t* slot_unknown, const int32_t* slot_contact, int contact,
+                              double* out) {
+  const int e = blockIdx.x;
+  __shared__ double red[3][256];
+  double dos = 0, ltr = 0, tr = 0;
+  for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
+    dos += gr[e * n + u].y;
+    if (gl) ltr += gl[e * n + u].y;
+  }
+  if (gl && sr)
+    for (int64_t k = threadIdx.x; k < ncs; k += blockDim.x)
+      if (slot_contact[k] == contact) tr += -2.0 * sr[e * ncs + k].y * gl[e * n + slot_unknown[k]].y;
+  red[0][threadIdx.x] = dos;
+  red[1][threadIdx.x] = tr;
+  red[2][threadIdx.x] = ltr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[3 * e + 0] = -red[0][0] / 3.14159265358979323846;
+    out[3 * e + 1] = red[1][0];
+    out[3 * e + 2] = red[2][0];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_observables(int64_t n_E, int64_t n, const c64* gr, const c64* gl, const c64* sr,
+                               int64_t ncs, const int64_t* slot_unknown, const int32_t* slot_contact,
+                               int contact, double* out, cudaStream_t s) {
+  if (n_E <= 0) return cudaSuccess;
+  k_observables<<<(unsigned)n_E, 256, 0, s>>>(n, gr, gl, sr, ncs, slot_unknown, slot_contact, contact, out);
+  return cudaGetLastError();
+}
 
 // ---- launchers -----------------------------------------------------------------------------------
 

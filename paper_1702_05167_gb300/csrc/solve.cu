@@ -102,6 +102,8 @@ struct DeviceState {
   void* io = nullptr;
   int64_t* poff = nullptr;
   int64_t pair_cap = 0;
+  int64_t* slot_unknown = nullptr;   // contact slot -> unknown (observables)
+  int32_t* slot_contact = nullptr;   // contact slot -> contact id
   cudaStream_t branch = nullptr;
   std::vector<void*> fixed;          // energy-independent allocations
 };
@@ -116,6 +118,8 @@ void device_state_free(DeviceState* d) {
   if (d->arena) cudaFree(d->arena);
   if (d->io) cudaFree(d->io);
   if (d->poff) cudaFree(d->poff);
+  if (d->slot_unknown) cudaFree(d->slot_unknown);
+  if (d->slot_contact) cudaFree(d->slot_contact);
   if (d->branch) cudaStreamDestroy(d->branch);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -715,6 +719,8 @@ int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
   }
   if (n_req > d->pair_cap) {
     if (d->poff) cudaFree(d->poff);
+  if (d->slot_unknown) cudaFree(d->slot_unknown);
+  if (d->slot_contact) cudaFree(d->slot_contact);
     d->poff = nullptr;
     d->pair_cap = 0;
     if (cudaMalloc((void**)&d->poff, (size_t)n_req * sizeof(int64_t)) != cudaSuccess) {
@@ -1192,5 +1198,38 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
       std::fclose(f);
     }
   }
+  return HSC_OK;
+}
+
+extern "C" int hsc_observables(hsc_t h, int64_t n_E, const hsc_c128* diag_gr, const hsc_c128* diag_gl,
+                               const hsc_c128* sigma_r, int32_t contact, double* out, void* cuda_stream) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (n_E < 0 || (n_E > 0 && (!diag_gr || !out))) return hsc_fail(h, HSC_ERR_ARG, "bad observables arguments");
+  if (contact < 0 || contact >= std::max(h->n_contacts, 1)) return hsc_fail(h, HSC_ERR_ARG, "contact out of range");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  int rc = get_state(h);
+  if (rc != HSC_OK) return rc;
+  DeviceState* d = h->dev;
+  const int64_t ncs = h->n_contact_unknowns;
+  if (!d->slot_unknown && ncs > 0) {
+    std::vector<int64_t> su;
+    std::vector<int32_t> sc;
+    for (int c = 0; c < h->n_contacts; ++c)
+      for (int64_t k = h->contact_ptr[c]; k < h->contact_ptr[c + 1]; ++k)
+        for (int o = 0; o < h->orb; ++o) {
+          su.push_back((int64_t)h->contact_sites[k] * h->orb + o);
+          sc.push_back(c);
+        }
+    cudaError_t e = upload(d, &d->slot_unknown, su);
+    if (e == cudaSuccess) e = upload(d, &d->slot_contact, sc);
+    if (e != cudaSuccess) return hsc_fail(h, HSC_ERR_CUDA, "upload contact slots");
+    // owned by `fixed` through upload(); do not free twice
+    d->fixed.pop_back();
+    d->fixed.pop_back();
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(launch_observables(n_E, h->n, reinterpret_cast<const c64*>(diag_gr),
+                        reinterpret_cast<const c64*>(diag_gl), reinterpret_cast<const c64*>(sigma_r), ncs,
+                        d->slot_unknown, d->slot_contact, contact, out, s));
   return HSC_OK;
 }

@@ -19,7 +19,9 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
 
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
            "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read",
-           "hsc_device_fp64_peaks", "hsc_last_error", "hsc_destroy"]
+           "hsc_device_fp64_peaks", "hsc_observables", "hsc_last_error", "hsc_destroy",
+           "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
+           "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF = 1, 2, 3, 4
 
 
@@ -89,6 +91,15 @@ def load():
                            ctypes.POINTER(hsc_tune_result)]
     L.hsc_set_option.argtypes = [vp, i32, i32]
     L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
+    L.hsc_observables.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp]
+    L.hsc_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32]
+    L.hsc_mlp_num_params.argtypes = [vp, ctypes.POINTER(i64)]
+    L.hsc_mlp_set_params.argtypes = [vp, vp]
+    L.hsc_mlp_get_params.argtypes = [vp, vp]
+    L.hsc_mlp_forward.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.hsc_mlp_loss_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.hsc_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+    L.hsc_mlp_destroy.argtypes = [vp]
     L.hsc_profile.argtypes = [vp, i32]
     L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(hsc_kernel_stat), i32, ctypes.POINTER(i32)]
     L.hsc_device_fp64_peaks.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
@@ -97,7 +108,9 @@ def load():
     L.hsc_destroy.argtypes = [vp]
     for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
                  "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile",
-                 "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_destroy"):
+                 "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_observables", "hsc_destroy",
+                 "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
+                 "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -247,6 +260,64 @@ def hsc_block_inverse_noalloc(n, batch, A, Ainv, stream=None):
     L.hsc_block_inverse_noalloc.restype = ctypes.c_int
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(None, L.hsc_block_inverse_noalloc(int(n), int(batch), _ptr(A), _ptr(Ainv), s))
+
+
+def hsc_observables(h, diag_gr, diag_gl, sigma_r, contact, out, stream=None):
+    """out: device float64 [n_E, 3] <- (DOS, T into `contact`, sum Im G^<) per energy."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(h, load().hsc_observables(h, int(diag_gr.shape[0]), _ptr(diag_gr), _ptr(diag_gl),
+                                     _ptr(sigma_r), int(contact), _ptr(out), s))
+
+
+class MLP:
+    """Owner of an hsc_mlp handle (include/hsc_mlp.h); buffers are torch CUDA float32 tensors."""
+
+    def __init__(self, n_in, width, hidden, n_out, max_batch):
+        L = load()
+        self.h = ctypes.c_void_p()
+        _check(None, L.hsc_mlp_create(ctypes.byref(self.h), n_in, width, hidden, n_out, max_batch))
+        n = ctypes.c_int64()
+        _check(None, L.hsc_mlp_num_params(self.h, ctypes.byref(n)))
+        self.n_params = n.value
+        self.shape = (n_in, width, hidden, n_out)
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(None, load().hsc_mlp_set_params(self.h, _ptr(p)))
+
+    def get_params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        _check(None, load().hsc_mlp_get_params(self.h, _ptr(p)))
+        return p
+
+    def forward(self, x, y, bf16=False, stream=None):
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        _check(None, load().hsc_mlp_forward(self.h, int(x.shape[0]), _ptr(x), _ptr(y),
+                                            1 if bf16 else 0, s))
+
+    def loss_grad(self, x, t, want_grad=False, stream=None):
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32) if want_grad else None
+        _check(None, load().hsc_mlp_loss_grad(self.h, int(x.shape[0]), _ptr(x), _ptr(t), _ptr(loss),
+                                              _ptr(g), s))
+        return (float(loss[0]), g) if want_grad else float(loss[0])
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        _check(None, load().hsc_mlp_adam(self.h, lr, beta1, beta2, eps, s))
+
+    def close(self):
+        if self.h:
+            load().hsc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hsc_last_error(h=None):
