@@ -24,6 +24,10 @@ struct GemmProb {
   int tiles_n;        // ceil(N / BN)
   int tile_start;     // first tile index of this problem in the flattened tile space
   int64_t a, b, c, d; // element offsets
+  // tensor-core engine only: operand images packed once per launch (TF32 hi/lo planes, 128 x 16
+  // core-matrix blocks of 32 KB); word offsets of the A and B images in the per-energy pack buffer
+  int tiles_m, ksteps, pack_start;   // pack_start: first pack block of this problem
+  int64_t pa, pb;
 };
 
 enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_H = 3 };   // none, transpose, conjugate, adjoint
@@ -39,11 +43,16 @@ struct GemmArgs {
   double ar, ai, br, bi;          // alpha, beta
   int opa, opb;
   double flops;                   // algorithmic real flops per energy (host bookkeeping)
+  int pack_blocks;                // tensor-core engine: 128x16 operand blocks to pack per energy
+  int64_t pack_words;             // tensor-core engine: pack buffer words needed per energy
 };
 
 // launchers (gemm_f64.cu, gemm_tc.cu)
 cudaError_t gemm_z(const GemmArgs& g, int n_energy, cudaStream_t s);
 cudaError_t gemm_tc(const GemmArgs& g, int n_energy, int* flag, cudaStream_t s);
+cudaError_t gemm_tc_packed(const GemmArgs& g, int n_energy, uint32_t* pack, int64_t pack_es, int* flag,
+                           cudaStream_t s);
+cudaError_t launch_wait_probe(double seconds, int* flag, cudaStream_t s);
 
 // Gauss-Jordan inversion problem: n x n matrix at element offset `off` (row stride ld) of a
 // per-energy array; pivots at piv_off of the per-energy pivot array; panel copy M (n x nb, row

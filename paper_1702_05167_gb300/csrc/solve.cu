@@ -51,9 +51,10 @@ struct DownLevel {
   GemmPair d[9]{};
 };
 
-enum KClass { K_GEMM = 0, K_GEMM_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
+enum KClass { K_GEMM = 0, K_GEMM_TC, K_SCHUR, K_SCHUR_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
               K_OUT, K_NCLASS };
-static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
+static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "schur_z_dmma",
+                                           "schur_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
                                            "assemble", "add_a", "lesser_fold", "gather", "out"};
 
 struct Prof {
@@ -90,6 +91,8 @@ struct DeviceState {
   std::vector<DownLevel> down;
   // per-energy strides (elements)
   int64_t aug_es = 0, sq_es = 0, x_es = 0, tt_es = 0, tz_es = 0, tn_es = 0, gjt_es = 0, piv_es = 0;
+  int64_t pk_es = 1;                 // tensor-core operand pack buffer (32-bit words per energy)
+  bool use_pack = true;              // HSC_MIXED: pack operands once per launch (else per tile)
   // workspace for `cap` energies
   int64_t cap = 0;
   void* arena = nullptr;
@@ -97,6 +100,7 @@ struct DeviceState {
       *X = nullptr, *T = nullptr, *Z = nullptr, *GUU = nullptr, *PUU = nullptr, *N = nullptr,
       *GJT = nullptr;
   int32_t* piv = nullptr;
+  uint32_t* PK = nullptr;
   // host-io staging, requested-pair offsets, batch branch stream
   int64_t io_cap = 0;
   void* io = nullptr;
@@ -153,6 +157,8 @@ struct GemmList {
   int tiles = 0, tiles128 = 0;
   int count = 0;
   double flops = 0;
+  int pack_blocks = 0;
+  int64_t pack_words = 0;
   GemmList(std::vector<GemmProb>& a, std::vector<GemmProb>& b)
       : all(a), all128(b), start(a.size()), start128(b.size()) {}
   void add(int M, int N, int K, int64_t a, int lda, int64_t b, int ldb, int64_t c, int ldc,
@@ -172,6 +178,13 @@ struct GemmList {
     q.tiles_n = (N + 127) / 128;
     q.tile_start = tiles128;
     tiles128 += ((M + 127) / 128) * q.tiles_n;
+    q.tiles_m = (M + 127) / 128;
+    q.ksteps = (K + 15) / 16;
+    q.pack_start = pack_blocks;
+    q.pa = pack_words;
+    q.pb = pack_words + (int64_t)q.tiles_m * q.ksteps * 8192;
+    pack_blocks += (q.tiles_m + q.tiles_n) * q.ksteps;
+    pack_words += (int64_t)(q.tiles_m + q.tiles_n) * q.ksteps * 8192;
     flops += 8.0 * M * N * K;
     all.push_back(p);
     all128.push_back(q);
@@ -190,6 +203,8 @@ struct GemmList {
     r.tc = g;
     r.tc.probs = reinterpret_cast<const GemmProb*>(start128);
     r.tc.total_tiles = tiles128;
+    r.tc.pack_blocks = pack_blocks;
+    r.tc.pack_words = pack_words;
     return r;
   }
 };
@@ -389,6 +404,17 @@ int build_schedule(hsc_ctx* h) {
     }
     D.d[8] = g9.args(OP_N, OP_H, 1, 0, 1, 0);
   }
+  {
+    int64_t pk = 1;
+    auto upd = [&](const GemmPair& g) { pk = std::max(pk, g.tc.pack_words); };
+    for (auto& U : d->up) {
+      upd(U.u1); upd(U.u2); upd(U.u3); upd(U.u4);
+      for (auto& st : U.steps) upd(st);
+    }
+    for (auto& D : d->down)
+      for (auto& g : D.d) upd(g);
+    d->pk_es = pk;
+  }
   d->tt_es = tt_max;
   d->tz_es = tz_max;
   d->tn_es = tn_max;
@@ -440,16 +466,17 @@ int build_schedule(hsc_ctx* h) {
   return HSC_OK;
 }
 
-int64_t bytes_per_energy(const DeviceState* d) {
+int64_t bytes_per_energy(const DeviceState* d, bool pack = false) {
   int64_t c = 4 * d->aug_es + 2 * d->sq_es + d->x_es + d->tt_es + 3 * d->tz_es + d->tn_es + d->gjt_es;
-  return c * (int64_t)sizeof(c64) + d->piv_es * 4;
+  return c * (int64_t)sizeof(c64) + d->piv_es * 4 + (pack ? d->pk_es * 4 : 0);
 }
 
-int ensure_arena(hsc_ctx* h, int64_t want) {
+int ensure_arena(hsc_ctx* h, int64_t want, bool pack) {
   DeviceState* d = h->dev;
-  if (d->cap >= want) return HSC_OK;
+  if (d->cap >= want && (!pack || d->PK)) return HSC_OK;
+  want = std::max(want, d->cap);
   if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->cap = 0; }
-  size_t bytes = (size_t)bytes_per_energy(d) * want + 64 * 256;
+  size_t bytes = (size_t)bytes_per_energy(d, pack) * want + 64 * 256;
   cudaError_t e = cudaMalloc(&d->arena, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -475,6 +502,7 @@ int ensure_arena(hsc_ctx* h, int64_t want) {
   d->N = (c64*)take(d->tn_es, 16);
   d->GJT = (c64*)take(d->gjt_es, 16);
   d->piv = (int32_t*)take(d->piv_es, 4);
+  d->PK = pack ? (uint32_t*)take(d->pk_es, 4) : nullptr;
   d->cap = want;
   return HSC_OK;
 }
@@ -527,10 +555,14 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
   const int64_t ncs = h->n_contact_unknowns;
   // ---- upward (Algorithm 1 first loop, Algorithm 2 fold) ----
   bool tc = false;   // current level's GEMMs on the tensor cores (mixed mode, below the top levels)
+  bool schur = false;   // the launch is Algorithm 1's Schur update (profiled separately)
   auto gemm = [&](const GemmArgs& gz, const GemmArgs& gt) -> int {
     if (gz.total_tiles <= 0) return HSC_OK;
-    if (tc) LAUNCH(K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
-    else LAUNCH(K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s));
+    if (tc && d->PK)
+      LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 2, gt.flops * ne, 0.0,
+             gemm_tc_packed(gt, ne, d->PK, d->pk_es, d->flag + 2, s));
+    else if (tc) LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
+    else LAUNCH(schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s));
     return HSC_OK;
   };
 #define GEMM(pair, ...)                                                   \
@@ -567,7 +599,9 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
     LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
            launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s));
     GEMM(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0);
+    schur = true;
     GEMM(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es);
+    schur = false;
     if (les && U.any_lesser) {
       GEMM(U.u3, d->L, d->aug_es, d->X, d->x_es, d->T, d->tt_es, d->L, d->aug_es);
       GEMM(U.u4, d->X, d->x_es, d->T, d->tt_es, d->Z, d->tz_es, nullptr, 0);
@@ -672,6 +706,7 @@ int get_state(hsc_ctx* h) {
     h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
     if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
     if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
+    if (const char* v = getenv("HSC_TC_PACK")) h->dev->use_pack = atoi(v) != 0;
   }
   DeviceState* d = h->dev;
   int cur = 0;
@@ -734,14 +769,15 @@ int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
 }
 
 // Sizes (and allocates) the workspace for waves of at most `wave` energies.
-int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out) {
+int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out, bool pack) {
   DeviceState* d = h->dev;
-  const int64_t per = bytes_per_energy(d);
+  pack = pack && d->use_pack;
+  const int64_t per = bytes_per_energy(d, pack);
   int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(byte_cap / per, 0));
   if (d->cap > 0) wave = std::max<int64_t>(std::min<int64_t>(n_E, d->cap), wave);
   if (wave <= 0) return hsc_fail(h, HSC_ERR_OOM, "one energy needs " + std::to_string(per >> 20) + " MiB of workspace");
   wave = std::min<int64_t>(wave, 65535);
-  int rc = ensure_arena(h, wave);
+  int rc = ensure_arena(h, wave, pack);
   if (rc != HSC_OK) return rc;
   *wave_out = wave;
   return HSC_OK;
@@ -794,7 +830,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
   if ((rc = upload_pairs(h, n_req, req_pairs)) != HSC_OK) return rc;
   DeviceState* d = h->dev;
   int64_t wave = 0;
-  if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave)) != HSC_OK) return rc;
+  if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave, precision == HSC_MIXED)) != HSC_OK) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (io_on_device) {
     rc = enqueue_device(h, n_E, wave, E, eta, sigma_r, sigma_less, precision, n_req, diag_gr, diag_gl,
@@ -932,9 +968,15 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   p.M = M; p.N = N; p.K = K;
   p.lda = lda; p.ldb = ldb; p.ldc = ldc; p.ldd = ldd;
   p.use_d = D ? 1 : 0;
-  const int tile = engine == 1 ? 128 : TILE;
+  const int tile = engine >= 1 ? 128 : TILE;
   p.tiles_n = (N + tile - 1) / tile;
   p.tile_start = 0;
+  p.tiles_m = (M + 127) / 128;
+  p.ksteps = (K + 15) / 16;
+  p.pack_start = 0;
+  p.pa = 0;
+  p.pb = (int64_t)p.tiles_m * p.ksteps * 8192;
+  const int64_t pack_words = (int64_t)(p.tiles_m + p.tiles_n) * p.ksteps * 8192;
   GemmProb* dp = nullptr;
   int* flag = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
@@ -946,12 +988,22 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   g.probs = dp; g.nprob = 1; g.total_tiles = ((M + tile - 1) / tile) * p.tiles_n;
   g.A = A; g.B = B; g.C = C; g.D = D;
   g.ar = ar; g.ai = ai; g.br = br; g.bi = bi; g.opa = opa; g.opb = opb;
-  cudaError_t e = engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s);
+  g.pack_blocks = (p.tiles_m + p.tiles_n) * p.ksteps;
+  g.pack_words = pack_words;
+  uint32_t* pk = nullptr;
+  if (engine == 2 && cudaMalloc(&pk, std::max<int64_t>(pack_words, 1) * 4) != cudaSuccess) {
+    cudaFree(dp);
+    cudaFree(flag);
+    return hsc_fail(nullptr, HSC_ERR_OOM, "cudaMalloc pack");
+  }
+  cudaError_t e = engine == 2 ? gemm_tc_packed(g, 1, pk, pack_words, flag, s)
+                  : engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s);
   int hf = 0;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(dp);
   cudaFree(flag);
+  if (pk) cudaFree(pk);
   if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, cudaGetErrorString(e));
   if (hf) return hsc_fail(nullptr, HSC_ERR_TIMEOUT, "tensor-core GEMM wait expired");
   return HSC_OK;
@@ -995,7 +1047,8 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
     if (rc == HSC_OK) rc = get_state(h);
     if (rc == HSC_OK) rc = upload_pairs(h, it.n_req, it.req_pairs);
     if (rc != HSC_OK) return item_fail(i, h, rc);
-    need[i] = (double)bytes_per_energy(h->dev) * (double)std::max<int64_t>(it.n_E, 1);
+    need[i] = (double)bytes_per_energy(h->dev, precision == HSC_MIXED && h->dev->use_pack) *
+              (double)std::max<int64_t>(it.n_E, 1);
     need_total += need[i];
   }
   const double budget = (double)budget_bytes();
@@ -1003,7 +1056,7 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
   for (int i = 0; i < n_items; ++i) {
     hsc_ctx* h = items[i].h;
     int64_t cap = (int64_t)(budget * need[i] / need_total);
-    int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i]);
+    int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i], precision == HSC_MIXED);
     if (rc != HSC_OK) return item_fail(i, h, rc);
     if (!h->dev->branch) {
       cudaError_t e = cudaStreamCreateWithFlags(&h->dev->branch, cudaStreamNonBlocking);
@@ -1231,5 +1284,19 @@ extern "C" int hsc_observables(hsc_t h, int64_t n_E, const hsc_c128* diag_gr, co
   CK(launch_observables(n_E, h->n, reinterpret_cast<const c64*>(diag_gr),
                         reinterpret_cast<const c64*>(diag_gl), reinterpret_cast<const c64*>(sigma_r), ncs,
                         d->slot_unknown, d->slot_contact, contact, out, s));
+  return HSC_OK;
+}
+
+extern "C" int hsc_debug_wait_timeout(double seconds) {
+  if (!(seconds > 0.0) || seconds > 2.0) return hsc_fail(nullptr, HSC_ERR_ARG, "seconds must be in (0, 2]");
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_OOM, "cudaMalloc");
+  cudaMemset(flag, 0, sizeof(int));
+  cudaError_t e = launch_wait_probe(seconds, flag, 0);
+  int hf = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(flag);
+  if (e != cudaSuccess) return hsc_fail(nullptr, HSC_ERR_CUDA, cudaGetErrorString(e));
+  if (hf) return hsc_fail(nullptr, HSC_ERR_TIMEOUT, "bounded device wait expired (as intended)");
   return HSC_OK;
 }

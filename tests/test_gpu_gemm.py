@@ -9,7 +9,8 @@ from paper_1702_05167_gb300 import hsc
 
 pytestmark = pytest.mark.gpu
 OPS = [(0, 0), (1, 0), (0, 1), (0, 2), (0, 3)]
-SHAPES = [(1, 1, 1), (5, 7, 3), (64, 64, 16), (130, 257, 33), (128, 128, 128), (300, 200, 517)]
+SHAPES = [(1, 1, 1), (5, 7, 3), (64, 64, 16), (130, 257, 33), (128, 128, 128), (300, 200, 517),
+          (70, 90, 0)]
 
 
 @pytest.fixture(scope="module")
@@ -58,6 +59,14 @@ def run(L, engine, oa, ob, M, N, K, seed):
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_fp64_engine(lib, oa, ob, M, N, K):
     assert run(lib, 0, oa, ob, M, N, K, M + N + K) <= 1e-14
+
+
+@pytest.mark.parametrize("oa,ob", OPS)
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_tcgen05_packed_engine(lib, oa, ob, M, N, K):
+    """Operands packed once into TF32 tile images and streamed with bulk async copies."""
+    err = run(lib, 2, oa, ob, M, N, K, M + N + K)
+    assert err <= 2e-6, err
 
 
 @pytest.mark.parametrize("oa,ob", OPS)
