@@ -132,7 +132,10 @@ typedef enum {
   HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 16)                   */
   HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
   HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
-  HSC_OPT_LEAF = 4            /* read only                                                      */
+  HSC_OPT_LEAF = 4,           /* read only                                                      */
+  HSC_OPT_COMPLEX_4M = 5      /* FP64 block products with 4 real products per complex product   */
+                              /* (default 0: 3 products, Im = (Ar+Ai)(Br+Bi) - ArBr - AiBi, 25 % */
+                              /* less FP64-pipe work, slightly larger rounding constant)        */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);

@@ -21,7 +21,8 @@ int hsc_debug_offset(hsc_t h, int32_t i, int64_t* aug, int64_t* sq, int64_t* x);
 /* hsc_debug_gemm -- one complex GEMM C = alpha op(A) op(B) + beta D on device buffers (row-major,
  *   complex128) through one of the solve's engines: engine 0 = FP64 tensor pipe (mma.sync f64),
  *   1 = tcgen05 3xTF32 (FP32 accumulation, operands converted per tile), 2 = the same products
- *   from operands packed once into TF32 tile images and streamed by bulk async copies. op: 0 none, 1 transpose, 2 conjugate, 3 adjoint
+ *   from operands packed once into TF32 tile images and streamed by bulk async copies, 3 = FP64
+ *   tensor pipe with 4 real products per complex product. op: 0 none, 1 transpose, 2 conjugate, 3 adjoint
  *   (engines support (opa, opb) in {(0,0), (1,0), (0,1), (0,2), (0,3)}). D may be NULL.
  *   Synchronises the stream. Errors: HSC_ERR_ARG, HSC_ERR_CUDA, HSC_ERR_TIMEOUT. */
 int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t M, int32_t N, int32_t K,

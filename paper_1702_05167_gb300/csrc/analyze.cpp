@@ -387,8 +387,19 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
     gr += n * m * m;              // Schur update S = S - A_Ui X
     gr += n * m * m + n * n * m;  // G_iU, G_ii
     if (cl[i].lesser) {
-      gl += n * n * m + n * m * m;                  // lesser fold T, Z
-      gl += (n * n * m + n * m * m) + (n * n * n + n * n * m) + n * n * (n + m);   // N, W
+      double w = n;   // rows of the lesser front that can be non-zero
+      bool leaf = cl[i].nchild == 0;
+      if (leaf) {     // leaves: diag(Sigma^<) on the hull of the own contact rows, L_iU = 0
+        int64_t lo = cl[i].n, hi = -1;
+        for (int64_t r = 0; r < cl[i].n; ++r)
+          if (P.own_contact[P.own_off[i] + r] >= 0) { lo = std::min(lo, r); hi = r; }
+        w = hi >= lo ? (double)(hi - lo + 1) : 0.0;
+        gl += w * w * m + w * m * m;                          // fold T, Z
+        gl += w * w * m + w * w * n + n * w * (n + m);        // N_iU, N_ii rows, W
+      } else {
+        gl += n * n * m + n * m * m;                  // lesser fold T, Z
+        gl += (n * n * m + n * m * m) + (n * n * n + n * n * m) + n * n * (n + m);   // N, W
+      }
     }
     gl += n * m * m + n * n * m;  // P_iU, P_ii
   }

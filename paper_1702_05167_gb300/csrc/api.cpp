@@ -185,6 +185,9 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
     case HSC_OPT_MIXED_GJ_FP64:
       h->opt_gj_fp64 = value != 0;
       break;
+    case HSC_OPT_COMPLEX_4M:
+      h->opt_4m = value != 0;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
@@ -200,6 +203,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_FP64_LEVELS: *value = h->opt_fp64_levels; break;
     case HSC_OPT_MIXED_GJ_FP64: *value = h->opt_gj_fp64; break;
     case HSC_OPT_LEAF: *value = h->leaf_max; break;
+    case HSC_OPT_COMPLEX_4M: *value = h->opt_4m; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   return HSC_OK;

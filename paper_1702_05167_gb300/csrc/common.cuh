@@ -48,7 +48,7 @@ struct GemmArgs {
 };
 
 // launchers (gemm_f64.cu, gemm_tc.cu)
-cudaError_t gemm_z(const GemmArgs& g, int n_energy, cudaStream_t s);
+cudaError_t gemm_z(const GemmArgs& g, int n_energy, cudaStream_t s, bool four_products = false);
 cudaError_t gemm_tc(const GemmArgs& g, int n_energy, int* flag, cudaStream_t s);
 cudaError_t gemm_tc_packed(const GemmArgs& g, int n_energy, uint32_t* pack, int64_t pack_es, int* flag,
                            cudaStream_t s);

@@ -31,6 +31,7 @@ struct hsc_ctx {
   int opt_nb = 16;            // Gauss-Jordan panel width
   int opt_fp64_levels = 2;    // HSC_MIXED: top tree levels kept on the FP64 pipe
   int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe
+  int opt_4m = 0;             // FP64 engine: 4 real products per complex product (default 3)
   int leaf_max = 0;           // last hsc_analyze leaf size
 };
 

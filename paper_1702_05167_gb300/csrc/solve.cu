@@ -76,6 +76,7 @@ struct DeviceState {
   int nb = 16;                       // Gauss-Jordan panel width
   int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
   bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
+  bool four_products = false;        // FP64 engine: 4 real products per complex product (else 3M)
   // energy-independent device arrays
   ClusterGlobal* cg = nullptr;
   LevelCluster* lcs = nullptr;
@@ -233,6 +234,22 @@ int build_schedule(hsc_ctx* h) {
   std::vector<GemmProb> gps, gps128;
   int64_t tt_max = 1, tz_max = 1, tn_max = 1, gjt_max = 1;
 
+  // leaves: the lesser front is diag(Sigma^<) on the own contact rows and L_iU = 0, so the leaf's
+  // lesser products only need the hull [c0, c1) of those rows (rows outside are exactly zero)
+  std::vector<int> hc0(nc, 0), hc1(nc, 0);
+  std::vector<char> leafl(nc, 0);
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = P.cl[i];
+    hc0[i] = 0;
+    hc1[i] = (int)c.n;
+    if (c.nchild == 0 && c.lesser) {
+      int lo = (int)c.n, hi = -1;
+      for (int64_t r = 0; r < c.n; ++r)
+        if (P.own_contact[P.own_off[i] + r] >= 0) { lo = std::min(lo, (int)r); hi = (int)r; }
+      if (hi >= lo) { hc0[i] = lo; hc1[i] = hi + 1; leafl[i] = 1; }
+    }
+  }
+
   auto base_lc = [&](int i) {
     const Cluster& c = P.cl[i];
     LevelCluster L{};
@@ -302,14 +319,24 @@ int build_schedule(hsc_ctx* h) {
       GemmList g3(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
-        if (L.lesser)
+        const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
+        if (!L.lesser) continue;
+        if (leafl[i])
+          g3.add(w, L.m, w, L.aug + (int64_t)c0 * (L.n + L.m) + c0, L.n + L.m, L.x + (int64_t)c0 * L.m, L.m,
+                 L.tt + (int64_t)c0 * L.m, L.m);
+        else
           g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.x, L.m, L.tt, L.m, L.aug + L.n, L.n + L.m, 1);
       }
       U.u3 = g3.args(OP_N, OP_C, 0.5, 0, -1, 0);
       GemmList g4(gps, gps128);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
-        if (L.lesser) g4.add(L.m, L.m, L.n, L.x, L.m, L.tt, L.m, L.tz, L.m);
+        const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
+        if (!L.lesser) continue;
+        if (leafl[i])
+          g4.add(L.m, L.m, w, L.x + (int64_t)c0 * L.m, L.m, L.tt + (int64_t)c0 * L.m, L.m, L.tz, L.m);
+        else
+          g4.add(L.m, L.m, L.n, L.x, L.m, L.tt, L.m, L.tz, L.m);
       }
       U.u4 = g4.args(OP_T, OP_N, 1, 0, 0, 0);
       const GJProb* gl = gjs.data() + U.gj;
@@ -362,33 +389,51 @@ int build_schedule(hsc_ctx* h) {
     GemmList g3(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      if (L.lesser) g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn + L.n, L.n + L.m);
+      const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
+      const int64_t ro = (int64_t)c0 * (L.n + L.m);
+      if (!L.lesser) continue;
+      if (leafl[i])
+        g3.add(w, L.m, w, L.aug + ro + c0, L.n + L.m, L.aug + ro + L.n, L.n + L.m, L.tn + ro + L.n, L.n + L.m);
+      else
+        g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn + L.n, L.n + L.m);
     }
     D.d[2] = g3.args(OP_N, OP_C, 1, 0, 0, 0);
     GemmList g4(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      if (L.lesser)
+      if (L.lesser && !leafl[ids[k]])   // L_iU = 0 on leaves
         g4.add(L.n, L.m, L.m, L.aug + L.n, L.n + L.m, L.tz, L.m, L.tn + L.n, L.n + L.m, L.tn + L.n, L.n + L.m, 1);
     }
     D.d[3] = g4.args(OP_N, OP_C, 1, 0, 1, 0);
     GemmList g5(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      if (L.lesser) g5.add(L.n, L.n, L.n, L.aug, L.n + L.m, L.aug, L.n + L.m, L.tn, L.n + L.m);
+      const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
+      const int64_t ro = (int64_t)c0 * (L.n + L.m);
+      if (!L.lesser) continue;
+      if (leafl[i])
+        g5.add(w, L.n, w, L.aug + ro + c0, L.n + L.m, L.aug + ro, L.n + L.m, L.tn + ro, L.n + L.m);
+      else
+        g5.add(L.n, L.n, L.n, L.aug, L.n + L.m, L.aug, L.n + L.m, L.tn, L.n + L.m);
     }
     D.d[4] = g5.args(OP_N, OP_C, 1, 0, 0, 0);
     GemmList g6(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      if (L.lesser)
+      if (L.lesser && !leafl[ids[k]])   // L_iU = 0 on leaves
         g6.add(L.n, L.n, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn, L.n + L.m, L.tn, L.n + L.m, 1);
     }
     D.d[5] = g6.args(OP_N, OP_H, 1, 0, 1, 0);
     GemmList g7(gps, gps128);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      if (L.lesser) g7.add(L.n, L.n + L.m, L.n, L.aug, L.n + L.m, L.tn, L.n + L.m, L.aug, L.n + L.m);
+      const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
+      if (!L.lesser) continue;
+      if (leafl[i])   // W = D^{-1}[:, c0:c1) N[c0:c1, :]
+        g7.add(L.n, L.n + L.m, w, L.aug + c0, L.n + L.m, L.tn + (int64_t)c0 * (L.n + L.m), L.n + L.m, L.aug,
+               L.n + L.m);
+      else
+        g7.add(L.n, L.n + L.m, L.n, L.aug, L.n + L.m, L.tn, L.n + L.m, L.aug, L.n + L.m);
     }
     D.d[6] = g7.args(OP_N, OP_N, 1, 0, 0, 0);
     GemmList g8(gps, gps128);
@@ -562,7 +607,7 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 2, gt.flops * ne, 0.0,
              gemm_tc_packed(gt, ne, d->PK, d->pk_es, d->flag + 2, s));
     else if (tc) LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
-    else LAUNCH(schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s));
+    else LAUNCH(schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s, d->four_products));
     return HSC_OK;
   };
 #define GEMM(pair, ...)                                                   \
@@ -704,6 +749,7 @@ int get_state(hsc_ctx* h) {
     h->dev->nb = h->opt_nb;
     h->dev->fp64_levels = h->opt_fp64_levels;
     h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
+    h->dev->four_products = h->opt_4m != 0;
     if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
     if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
     if (const char* v = getenv("HSC_TC_PACK")) h->dev->use_pack = atoi(v) != 0;
@@ -968,7 +1014,7 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   p.M = M; p.N = N; p.K = K;
   p.lda = lda; p.ldb = ldb; p.ldc = ldc; p.ldd = ldd;
   p.use_d = D ? 1 : 0;
-  const int tile = engine >= 1 ? 128 : TILE;
+  const int tile = (engine == 1 || engine == 2) ? 128 : TILE;
   p.tiles_n = (N + tile - 1) / tile;
   p.tile_start = 0;
   p.tiles_m = (M + 127) / 128;
@@ -997,7 +1043,7 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
     return hsc_fail(nullptr, HSC_ERR_OOM, "cudaMalloc pack");
   }
   cudaError_t e = engine == 2 ? gemm_tc_packed(g, 1, pk, pack_words, flag, s)
-                  : engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s);
+                  : engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s, engine == 3);
   int hf = 0;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);

@@ -7,10 +7,10 @@ the plain selected-inversion solve is both its fallback and the judge of every i
 * Network: input (E, 16 disorder features) -> 3 x 256 GELU -> (log10 T, DOS per site), trained on
   the GPU by the library's own forward/backward/Adam kernels (include/hsc_mlp.h), FP32 weights,
   BF16 inference.
-* Grid: the surrogate's T(E) on a fine grid gives the trapezoid rule's local error density
-  |T''| h^2; points are placed at equal quantiles of rho = |T''|^(1/3)/mean + floor (equidistributing
-  that error; the predicted DOS is reported but not used: on these devices it is dominated by
-  interior levels of width eta that no energy grid resolves), then the real solve runs on them.
+* Grid: the surrogate's T(E) and DOS(E) on a fine grid give the trapezoid rule's local error
+  densities |T''| h^2 and |DOS''| h^2; points are placed at equal quantiles of
+  rho = |T''|^(1/3)/mean + |DOS''|^(1/3)/mean + floor (equidistributing those errors), then the real
+  solve runs on them.
 * Judge: integrals (current ~ int T dE, electron count ~ int sum Im G^< dE / 2 pi, int DOS dE) on the
   adaptive grid and on a uniform grid with the same number of points are compared with a dense
   uniform reference computed by the same solver.
@@ -141,15 +141,17 @@ class Surrogate:
         self.net.close()
 
 
-def adaptive_grid(sur, feats, n_points, fine=8192, floor=0.5, window=WINDOW):
-    """Energies at equal quantiles of rho = |T''|^(1/3)/mean + floor, with T the surrogate's
-    prediction on a fine uniform grid (endpoints always included)."""
+def adaptive_grid(sur, feats, n_points, fine=8192, floor=1.0, window=WINDOW):
+    """Energies at equal quantiles of rho = |T''|^(1/3)/mean + |D''|^(1/3)/mean + floor, with T
+    and D the surrogate's transmission and DOS on a fine uniform grid (endpoints included)."""
     Ef = np.linspace(window[0], window[1], fine)
     pred = sur.predict(np.column_stack([Ef, np.tile(feats, (fine, 1))]))
     T = 10.0 ** pred[:, 0]
+    Dn = pred[:, 1]
     h = Ef[1] - Ef[0]
-    a = np.abs(np.gradient(np.gradient(T, h), h)) ** (1 / 3)
-    rho = a / max(a.mean(), 1e-300) + floor
+    d2 = lambda y: np.abs(np.gradient(np.gradient(y, h), h)) ** (1 / 3)
+    a, b = d2(T), d2(Dn)
+    rho = a / max(a.mean(), 1e-300) + b / max(b.mean(), 1e-300) + floor
     cdf = np.concatenate([[0.0], np.cumsum(0.5 * (rho[1:] + rho[:-1]) * h)])
     cdf /= cdf[-1]
     return np.interp(np.linspace(0, 1, n_points), cdf, Ef)

@@ -58,7 +58,15 @@ def run(L, engine, oa, ob, M, N, K, seed):
 @pytest.mark.parametrize("oa,ob", OPS)
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_fp64_engine(lib, oa, ob, M, N, K):
-    assert run(lib, 0, oa, ob, M, N, K, M + N + K) <= 1e-14
+    """3M products: the imaginary part is a difference of products, bounded by ~eps K (|Ar|+|Ai|)
+    (|Br|+|Bi|); asserted at 1e-13 of |alpha||A||B| + |beta D| componentwise."""
+    assert run(lib, 0, oa, ob, M, N, K, M + N + K) <= 1e-13
+
+
+@pytest.mark.parametrize("oa,ob", OPS)
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_fp64_engine_four_products(lib, oa, ob, M, N, K):
+    assert run(lib, 3, oa, ob, M, N, K, M + N + K) <= 1e-14
 
 
 @pytest.mark.parametrize("oa,ob", OPS)
