@@ -133,9 +133,16 @@ typedef enum {
   HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
   HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
   HSC_OPT_LEAF = 4,           /* read only                                                      */
-  HSC_OPT_COMPLEX_4M = 5      /* FP64 block products with 4 real products per complex product   */
+  HSC_OPT_COMPLEX_4M = 5,     /* FP64 block products with 4 real products per complex product   */
                               /* (default 0: 3 products, Im = (Ar+Ai)(Br+Bi) - ArBr - AiBi, 25 % */
                               /* less FP64-pipe work, slightly larger rounding constant)        */
+  HSC_OPT_FP64_ENGINE = 6     /* engine of the FP64-accurate block products: 0 (default) picks  */
+                              /* per product list by a cost model, 1 = FP64 pipe only, 2 = FP64 */
+                              /* emulation on the BF16 tensor cores wherever K > 0. The         */
+                              /* emulation splits each real operand exactly into eight 7-bit    */
+                              /* slices (power-of-two row / column scales) and accumulates the  */
+                              /* slice products exactly; its error per K value is below         */
+                              /* 2^-52.8 times the two scales, at the level of FP64 rounding.   */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);

@@ -22,7 +22,9 @@ int hsc_debug_offset(hsc_t h, int32_t i, int64_t* aug, int64_t* sq, int64_t* x);
  *   complex128) through one of the solve's engines: engine 0 = FP64 tensor pipe (mma.sync f64),
  *   1 = tcgen05 3xTF32 (FP32 accumulation, operands converted per tile), 2 = the same products
  *   from operands packed once into TF32 tile images and streamed by bulk async copies, 3 = FP64
- *   tensor pipe with 4 real products per complex product. op: 0 none, 1 transpose, 2 conjugate, 3 adjoint
+ *   tensor pipe with 4 real products per complex product, 4 = FP64 emulation on the BF16 tensor
+ *   cores (tcgen05 kind::f16, operands split exactly into eight 7-bit slices, error below
+ *   2^-50 K max|row of op(A)| max|column of op(B)| per real product). op: 0 none, 1 transpose, 2 conjugate, 3 adjoint
  *   (engines support (opa, opb) in {(0,0), (1,0), (0,1), (0,2), (0,3)}). D may be NULL.
  *   Synchronises the stream. Errors: HSC_ERR_ARG, HSC_ERR_CUDA, HSC_ERR_TIMEOUT. */
 int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t M, int32_t N, int32_t K,

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhsc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cpp", "analyze.cpp", "solve.cu", "kernels.cu", "gemm_f64.cu", "gemm_tc.cu", "peak.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["api.cpp", "analyze.cpp", "solve.cu", "kernels.cu", "gemm_f64.cu", "gemm_tc.cu", "gemm_oz.cu", "peak.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC,
           "-I", os.path.join(os.path.dirname(HERE), "include")]

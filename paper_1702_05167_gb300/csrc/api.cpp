@@ -188,6 +188,10 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
     case HSC_OPT_COMPLEX_4M:
       h->opt_4m = value != 0;
       break;
+    case HSC_OPT_FP64_ENGINE:
+      if (value < 0 || value > 2) return hsc_fail(h, HSC_ERR_ARG, "engine must be 0, 1 or 2");
+      h->opt_fp64_engine = value;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
@@ -204,6 +208,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_MIXED_GJ_FP64: *value = h->opt_gj_fp64; break;
     case HSC_OPT_LEAF: *value = h->leaf_max; break;
     case HSC_OPT_COMPLEX_4M: *value = h->opt_4m; break;
+    case HSC_OPT_FP64_ENGINE: *value = h->opt_fp64_engine; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   return HSC_OK;

@@ -28,6 +28,8 @@ struct GemmProb {
   // core-matrix blocks of 32 KB); word offsets of the A and B images in the per-energy pack buffer
   int tiles_m, ksteps, pack_start;   // pack_start: first pack block of this problem
   int64_t pa, pb;
+  // FP64-emulation engine only: offsets of the row scales of op(A) and column scales of op(B)
+  int64_t sa, sb;
 };
 
 enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_H = 3 };   // none, transpose, conjugate, adjoint
@@ -45,6 +47,8 @@ struct GemmArgs {
   double flops;                   // algorithmic real flops per energy (host bookkeeping)
   int pack_blocks;                // tensor-core engine: 128x16 operand blocks to pack per energy
   int64_t pack_words;             // tensor-core engine: pack buffer words needed per energy
+                                  // (FP64-emulation engine: BF16 slice values per energy)
+  int64_t scale_vals;             // FP64-emulation engine: scale doubles per energy
 };
 
 // launchers (gemm_f64.cu, gemm_tc.cu)
@@ -53,6 +57,11 @@ cudaError_t gemm_tc(const GemmArgs& g, int n_energy, int* flag, cudaStream_t s);
 cudaError_t gemm_tc_packed(const GemmArgs& g, int n_energy, uint32_t* pack, int64_t pack_es, int* flag,
                            cudaStream_t s);
 cudaError_t launch_wait_probe(double seconds, int* flag, cudaStream_t s);
+// FP64-emulation engine (gemm_oz.cu): oz_layout fills the tile, pack and scale layout of a problem
+// and advances the list's running totals; gemm_oz packs the slices and runs the GEMM.
+void oz_layout(GemmProb& p, int& pack_blocks, int& tiles, int64_t& slice_vals, int64_t& scale_vals);
+cudaError_t gemm_oz(const GemmArgs& g, int n_energy, uint16_t* slices, int64_t slice_es, double* scales,
+                    int64_t scale_es, int* flag, cudaStream_t s);
 
 // Gauss-Jordan inversion problem: n x n matrix at element offset `off` (row stride ld) of a
 // per-energy array; pivots at piv_off of the per-energy pivot array; panel copy M (n x nb, row

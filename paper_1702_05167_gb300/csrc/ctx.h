@@ -32,6 +32,7 @@ struct hsc_ctx {
   int opt_fp64_levels = 2;    // HSC_MIXED: top tree levels kept on the FP64 pipe
   int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe
   int opt_4m = 0;             // FP64 engine: 4 real products per complex product (default 3)
+  int opt_fp64_engine = 0;    // FP64-accurate products: 0 cost model, 1 FP64 pipe, 2 emulation
   int leaf_max = 0;           // last hsc_analyze leaf size
 };
 

@@ -1,0 +1,461 @@
+// Complex128 GEMM at FP64 accuracy on the BF16 tensor cores (tcgen05 kind::f16) by exact operand
+// splitting (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications", Numerical
+// Algorithms 59, 2012).
+//
+// C = alpha op(A) op(B) + beta D. The complex product is taken as three real products (3M):
+//     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),
+//     C = beta D + alpha [(1 - i) T0 + (-1 - i) T1 + i T2].
+// Each real product X Y (X: M x K, Y: K x N) is evaluated exactly up to a bounded truncation:
+//   * row i of X gets the power of two sigma_i > max_k |X_ik|, column j of Y likewise tau_j;
+//   * |X_ik| / sigma_i, a number in [0, 1), is truncated to 56 fraction bits and cut into OZ_S = 8
+//     slices of 7 bits; a slice t_s in [-127, 127] (sign of X_ik) is exact in BF16, and
+//         X_ik = sigma_i (sum_s t_s 2^(-7 s) + delta),  |delta| < 2^-56;
+//     the slicing works on the FP64 bit pattern (integer shifts only: GB300's FP64 pipe is slow);
+//   * a slice product t_s u_r is an integer below 2^14 and carries the weight 2^(-7 (s + r)); the
+//     products of one diagonal d = s + r (d <= OZ_S + 1: 36 pairs) accumulate in one FP32 tensor-
+//     memory accumulator, exact for 128 K values (at most 8 pairs: 8 * 127^2 * 128 < 2^24); every
+//     128 K values the 8 accumulators are drained into FP64 registers with their weights;
+//   * per K value the error is below 2^-52.8 sigma_i tau_j: 2 * 2^-56 from the truncation and
+//     2^-53.1 from the dropped diagonals d >= 10 (7 * 127^2 * 2^-70 for d = 10, less beyond).
+// Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
+// op(A) (all 8 slices, 32 KB) and a 64 x 16 block of op(B)^T (16 KB) in the K-major core-matrix
+// layout the MMA reads, for each of the three real operands (re, im, re + im).
+// Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
+// real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
+// counts), warp 1 issues the 36 MMAs of each K step, warps 2-9 drain the accumulators every 8 K steps
+// and, after the last chunk of a real product, add its share to C (read-modify-write by the owning
+// thread, so C may alias D). Every mbarrier wait is bounded; on expiry the kernel raises the flag,
+// waits (bounded) for its own copies, frees tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hsc {
+namespace {
+
+constexpr int OZ_S = 8;                  // slices per operand
+constexpr int OZ_BITS = 7;               // bits per slice
+constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // fraction bits kept (56)
+constexpr int OZ_ND = OZ_S;              // accumulated diagonals d = 2 .. OZ_S + 1
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;
+constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (all slices)
+constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_DRAIN = 8;              // K steps per drain (128 K values)
+constexpr uint32_t OZ_TMEM_COLS = 512;   // 8 accumulators x 64 columns
+constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
+constexpr int OZ_DRAIN_WARPS = 8;      // two per TMEM lane quadrant, 32 columns each
+constexpr int OZ_DCOLS = OZ_BN / 2;
+constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;
+constexpr int OZP_THREADS = 256;
+
+static_assert(OZ_ND * OZ_BN <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
+static_assert((long long)OZ_S * 127 * 127 * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
+
+__device__ __forceinline__ uint32_t oz_su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long oz_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, unsigned long long limit = OZ_WAIT_NS) {
+  const unsigned long long t0 = oz_timer();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (oz_timer() - t0 > limit) return false;
+  }
+}
+
+// element (r, k) of a rows x 16 K-major BF16 block: core matrices of 8 rows x 16 B (8 values); the
+// two K-adjacent core matrices are 128 B apart, adjacent 8-row groups 256 B apart
+__device__ __forceinline__ int oz_cidx(int r, int k) {
+  return (((r >> 3) * 2 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = 256;
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);   // no swizzle, version 1
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ int oz_expo(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// real operand v (0: re, 1: im, 2: re + im) of a complex value after the op's conjugation
+template <bool CONJ>
+__device__ __forceinline__ double oz_part(c64 x, int v) {
+  const double im = CONJ ? -x.y : x.y;
+  return v == 0 ? x.x : (v == 1 ? im : x.x + im);
+}
+
+// One CTA per (problem, side, real operand, tile): side A = 128 rows of op(A), side B = 64 rows of
+// op(B)^T (columns of op(B)). Layout per problem and energy (BF16 values):
+//   A images at pa: [v][tile_m][kstep][slice][128 x 16],  B images at pb: [v][tile_n][kstep][slice][64 x 16];
+//   scales (doubles) at sa: [v][tiles_m * 128],  at sb: [v][tiles_n * 64].
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* slices, int64_t slice_es,
+                                                         double* scales, int64_t scale_es) {
+  const int e = blockIdx.y;
+  const int blk = blockIdx.x;
+  int lo = 0, hi = g.nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.probs[mid].pack_start <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProb P = g.probs[lo];
+  int b = blk - P.pack_start;
+  const bool isA = b < 3 * P.tiles_m;
+  if (!isA) b -= 3 * P.tiles_m;
+  const int ntile = isA ? P.tiles_m : P.tiles_n;
+  const int v = b / ntile, tile = b % ntile;
+  const int rows = isA ? OZ_BM : OZ_BN;
+  const int row0 = tile * rows;
+  const int nrow = isA ? P.M : P.N;
+  const int K = P.K, ks = P.ksteps, Kp = ks * OZ_BK;
+  const c64* X = reinterpret_cast<const c64*>(isA ? g.A : g.B) + e * (isA ? g.a_es : g.b_es) + (isA ? P.a : P.b);
+  const int ld = isA ? P.lda : P.ldb;
+  // row r of op(A) (or of op(B)^T) is contiguous in memory for op(A) in {N, C} and op(B) in {T, H}
+  const bool krun = isA ? (OPA == OP_N || OPA == OP_C) : (OPB == OP_T || OPB == OP_H);
+  const bool conj = isA ? (OPA == OP_C || OPA == OP_H) : (OPB == OP_C || OPB == OP_H);
+  auto value = [&](int r, int k) -> double {
+    const c64 x = krun ? X[(int64_t)r * ld + k] : X[(int64_t)k * ld + r];
+    return conj ? oz_part<true>(x, v) : oz_part<false>(x, v);
+  };
+  uint16_t* dst = slices + e * slice_es +
+                  (isA ? P.pa + ((int64_t)v * P.tiles_m + tile) * ks * OZ_ABLK
+                       : P.pb + ((int64_t)v * P.tiles_n + tile) * ks * OZ_BBLK);
+  double* sc = scales + e * scale_es + (isA ? P.sa + (int64_t)v * P.tiles_m * OZ_BM
+                                            : P.sb + (int64_t)v * P.tiles_n * OZ_BN) + row0;
+  __shared__ int s_e[OZ_BM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int r = tid; r < rows; r += OZP_THREADS) s_e[r] = 0;
+  __syncthreads();
+  // largest biased exponent per row (0 for a row of zeros)
+  if (krun) {
+    for (int r = warp; r < rows; r += OZP_THREADS / 32) {
+      int ex = 0;
+      if (row0 + r < nrow)
+        for (int k = lane; k < K; k += 32) ex = max(ex, oz_expo(value(row0 + r, k)));
+      ex = (int)__reduce_max_sync(0xffffffffu, (unsigned)ex);
+      if (lane == 0) s_e[r] = ex;
+    }
+  } else {
+    const int phases = OZP_THREADS / rows;
+    const int r = tid % rows, ph = tid / rows;
+    int ex = 0;
+    if (row0 + r < nrow)
+      for (int k = ph; k < K; k += phases) ex = max(ex, oz_expo(value(row0 + r, k)));
+    atomicMax(&s_e[r], ex);
+  }
+  __syncthreads();
+  // sigma = 2^(E - 1022) > |x| for every x of the row with biased exponent <= E
+  for (int r = tid; r < rows; r += OZP_THREADS) sc[r] = s_e[r] > 0 ? ldexp(1.0, s_e[r] - 1022) : 0.0;
+  const int plane = rows * OZ_BK;
+  const int64_t blkv = isA ? OZ_ABLK : OZ_BBLK;
+  const int total = rows * Kp;
+  for (int i = tid; i < total; i += OZP_THREADS) {
+    const int r = krun ? i / Kp : i % rows;
+    const int k = krun ? i % Kp : i / rows;
+    const int gr = row0 + r;
+    const double x = (gr < nrow && k < K) ? value(gr, k) : 0.0;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    // m = floor(|x| / sigma * 2^56): |x| = mant 2^(ex - 1075), sigma = 2^(E - 1022), so the 53-bit
+    // significand moves right by E - ex + 52 - 56 + 1 (a left shift of at most 3 when ex = E)
+    unsigned long long m = 0;
+    const int shift = s_e[r] - ex + (52 - OZ_FRAC + 1);
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    if (ex > 0 && shift < 64) m = shift >= 0 ? mant >> shift : mant << (-shift);
+    const uint32_t sgn = (uint32_t)(bits >> 63) << 15;
+    uint16_t* o = dst + (int64_t)(k / OZ_BK) * blkv + oz_cidx(r, k % OZ_BK);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const uint32_t t = (uint32_t)(m >> (OZ_FRAC - OZ_BITS * (s + 1))) & 127u;
+      // t as an FP32 value (exact: t < 2^23), whose upper half is its exact BF16 encoding
+      const float f = __uint_as_float(0x4B000000u | t) - 8388608.0f;
+      o[s * plane] = (uint16_t)((__float_as_uint(f) >> 16) | sgn);
+    }
+  }
+}
+
+struct __align__(128) OzSmem {
+  uint16_t a[OZ_STAGES][OZ_ABLK];
+  uint16_t b[OZ_STAGES][OZ_BBLK];
+  unsigned long long full[OZ_STAGES];
+  unsigned long long empty[OZ_STAGES];
+  unsigned long long acc_full;    // MMA -> drain: a chunk of K steps is in the accumulators
+  unsigned long long acc_empty;   // drain -> MMA: accumulators read
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void oz_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void oz_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* scales, int64_t scale_es,
+          int* flag) {
+  extern __shared__ unsigned char smem_raw[];
+  OzSmem& sm = *reinterpret_cast<OzSmem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int e = blockIdx.y;
+  int lo = 0, hi = g.nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.probs[mid].tile_start <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProb P = g.probs[lo];
+  const int t = blockIdx.x - P.tile_start;
+  const int tm = t / P.tiles_n, tn = t % P.tiles_n;
+  const int ks = P.ksteps;
+  const int nchunk = (ks + OZ_DRAIN - 1) / OZ_DRAIN;   // per real product
+  const uint16_t* sl = slices + e * slice_es;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_su32(&sm.tmem)),
+                 "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.acc_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(&sm.acc_empty)), "r"(OZ_DRAIN_WARPS));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    sm.abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sm.tmem;
+  // kind::f16 with BF16 A and B, FP32 D, both K-major, M = 128, N = 64
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+  constexpr uint32_t ABYTES = OZ_ABLK * 2, BBYTES = OZ_BBLK * 2;
+  volatile int* abort_flag = &sm.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {   // producer: the K steps of the three real products in sequence
+      const int nsteps = 3 * ks;
+      for (int s = 0; s < nsteps; ++s) {
+        const int st = s % OZ_STAGES;
+        if (s >= OZ_STAGES && !oz_wait(oz_su32(&sm.empty[st]), (uint32_t)((s / OZ_STAGES - 1) & 1))) {
+          atomicExch(flag, 3);
+          *abort_flag = 1;
+          break;
+        }
+        const int v = s / ks, kk = s % ks;
+        const uint16_t* pa = sl + P.pa + (((int64_t)v * P.tiles_m + tm) * ks + kk) * OZ_ABLK;
+        const uint16_t* pb = sl + P.pb + (((int64_t)v * P.tiles_n + tn) * ks + kk) * OZ_BBLK;
+        const uint32_t fb = oz_su32(&sm.full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ABYTES + BBYTES)
+                     : "memory");
+        oz_bulk(oz_su32(&sm.a[st][0]), pa, ABYTES, fb);
+        oz_bulk(oz_su32(&sm.b[st][0]), pb, BBYTES, fb);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      bool ok = true;
+      for (int c = 0; c < 3 * nchunk && ok; ++c) {
+        if (c > 0 && !oz_wait(oz_su32(&sm.acc_empty), (uint32_t)((c - 1) & 1))) {
+          atomicExch(flag, 3);
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int v = c / nchunk, cc = c % nchunk;
+        const int s0 = v * ks + cc * OZ_DRAIN, s1 = v * ks + min(ks, (cc + 1) * OZ_DRAIN);
+        for (int s = s0; s < s1; ++s) {
+          const int st = s % OZ_STAGES;
+          if (!oz_wait(oz_su32(&sm.full[st]), (uint32_t)((s / OZ_STAGES) & 1))) {
+            atomicExch(flag, 3);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = oz_su32(&sm.a[st][0]), b0 = oz_su32(&sm.b[st][0]);
+#pragma unroll
+          for (int si = 0; si < OZ_S; ++si)
+#pragma unroll
+            for (int ri = 0; ri < OZ_S - si; ++ri) {   // s + r <= OZ_S + 1 (1-based slices)
+              // the first MMA of a chunk into diagonal si + ri is the one with si = 0
+              const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
+              oz_mma(tmem + (si + ri) * OZ_BN, oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)),
+                     oz_desc(b0 + ri * (OZ_BN * OZ_BK * 2)), idesc, acc);
+            }
+          oz_commit(oz_su32(&sm.empty[st]));
+        }
+        oz_commit(oz_su32(&sm.acc_full));   // also releases the drain warps after an abort
+      }
+    }
+  } else {   // warps 2-9: drain, TMEM lane quadrant = warp % 4, column half = (warp - 2) / 4
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int row = tm * OZ_BM + quad * 32 + lane;
+    c64* C = reinterpret_cast<c64*>(g.C) + e * g.c_es + P.c;
+    const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
+    const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
+    const int col0 = tn * OZ_BN + half * OZ_DCOLS;
+    double acc64[OZ_DCOLS];
+#pragma unroll
+    for (int j = 0; j < OZ_DCOLS; ++j) acc64[j] = 0.0;
+    if (ks == 0 && row < P.M) {   // C = beta D
+      for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
+        c64 o = make_double2(0.0, 0.0);
+        if (use_d) {
+          const c64 dv = D[(int64_t)row * P.ldd + col0 + j];
+          o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
+        }
+        C[(int64_t)row * P.ldc + col0 + j] = o;
+      }
+    }
+    for (int c = 0; c < 3 * nchunk; ++c) {
+      bool got = oz_wait(oz_su32(&sm.acc_full), (uint32_t)(c & 1));
+      got = __all_sync(0xffffffffu, got);   // warp-uniform before the .sync.aligned TMEM loads
+      if (!got) {
+        if (lane == 0) atomicExch(flag, 3);
+        break;
+      }
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int dg = 0; dg < OZ_ND; ++dg) {
+        const double w = __longlong_as_double((long long)(1023 - OZ_BITS * (dg + 2)) << 52);   // 2^(-7(dg+2))
+#pragma unroll
+        for (int c0 = 0; c0 < OZ_DCOLS; c0 += 16) {
+          uint32_t r[16];
+          const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + dg * OZ_BN + half * OZ_DCOLS + c0;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                "=r"(r[14]), "=r"(r[15])
+              : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc64[c0 + j] = fma(w, (double)__uint_as_float(r[j]), acc64[c0 + j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty)) : "memory");
+      const int v = c / nchunk;
+      if (c % nchunk == nchunk - 1) {   // real product v complete: C += kappa_v T_v
+        // kappa_0 = alpha (1 - i), kappa_1 = alpha (-1 - i), kappa_2 = alpha i
+        const double kr = v == 0 ? g.ar + g.ai : (v == 1 ? g.ai - g.ar : -g.ai);
+        const double ki = v == 0 ? g.ai - g.ar : (v == 1 ? -g.ar - g.ai : g.ar);
+        if (row < P.M) {
+          const double sr = scales[e * scale_es + P.sa + (int64_t)v * P.tiles_m * OZ_BM + row];
+          const double* scn = scales + e * scale_es + P.sb + (int64_t)v * P.tiles_n * OZ_BN + col0;   // col0 includes the tile
+          c64* crow = C + (int64_t)row * P.ldc + col0;
+          const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
+#pragma unroll
+          for (int j = 0; j < OZ_DCOLS; ++j) {
+            if (col0 + j < P.N) {
+              const double tv = acc64[j] * sr * scn[j];
+              c64 o;
+              if (v == 0) {
+                o = make_double2(0.0, 0.0);
+                if (use_d) {
+                  const c64 dv = drow[j];
+                  o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
+                }
+              } else {
+                o = crow[j];
+              }
+              o.x = fma(kr, tv, o.x);
+              o.y = fma(ki, tv, o.y);
+              crow[j] = o;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < OZ_DCOLS; ++j) acc64[j] = 0.0;
+      }
+    }
+  }
+  // copies still in flight after an abort: wait (bounded) for the stages the producer armed
+  if (tid == 0 && *abort_flag)
+    for (int s = 0; s < OZ_STAGES; ++s) oz_wait(oz_su32(&sm.full[s]), 0u, 100000000ull);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+}
+
+}  // namespace
+
+void oz_layout(GemmProb& p, int& pack_blocks, int& tiles, int64_t& slice_vals, int64_t& scale_vals) {
+  p.tiles_m = (p.M + OZ_BM - 1) / OZ_BM;
+  p.tiles_n = (p.N + OZ_BN - 1) / OZ_BN;
+  p.ksteps = (p.K + OZ_BK - 1) / OZ_BK;
+  p.tile_start = tiles;
+  tiles += p.tiles_m * p.tiles_n;
+  p.pack_start = pack_blocks;
+  pack_blocks += p.ksteps > 0 ? 3 * (p.tiles_m + p.tiles_n) : 0;
+  p.pa = slice_vals;
+  p.pb = slice_vals + 3LL * p.tiles_m * p.ksteps * OZ_ABLK;
+  slice_vals = p.pb + 3LL * p.tiles_n * p.ksteps * OZ_BBLK;
+  p.sa = scale_vals;
+  p.sb = scale_vals + 3LL * p.tiles_m * OZ_BM;
+  scale_vals = p.sb + 3LL * p.tiles_n * OZ_BN;
+}
+
+cudaError_t gemm_oz(const GemmArgs& g, int n_energy, uint16_t* slices, int64_t slice_es, double* scales,
+                    int64_t scale_es, int* flag, cudaStream_t s) {
+  if (g.total_tiles <= 0 || n_energy <= 0) return cudaSuccess;
+  if (g.pack_blocks > 0) {
+    dim3 pgrid(g.pack_blocks, n_energy);
+#define HSC_OZ_CASE(a, b)                                                                       \
+    if (g.opa == a && g.opb == b)                                                               \
+      k_oz_pack<a, b><<<pgrid, OZP_THREADS, 0, s>>>(g, slices, slice_es, scales, scale_es); else
+    HSC_OZ_CASE(OP_N, OP_N)
+    HSC_OZ_CASE(OP_T, OP_N)
+    HSC_OZ_CASE(OP_N, OP_T)
+    HSC_OZ_CASE(OP_N, OP_C)
+    HSC_OZ_CASE(OP_N, OP_H)
+    return cudaErrorInvalidValue;
+#undef HSC_OZ_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t sm = sizeof(OzSmem) + 128;
+  cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gemm_oz<<<dim3(g.total_tiles, n_energy), OZ_THREADS, sm, s>>>(g, slices, slice_es, scales, scale_es, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace hsc

@@ -27,6 +27,8 @@ namespace hsc {
 struct GemmPair {
   GemmArgs z;    // 64x64 tiles, FP64 tensor pipe (gemm_z)
   GemmArgs tc;   // 128x128 tiles, tcgen05 3xTF32 (gemm_tc)
+  GemmArgs oz;   // 128x64 tiles, FP64 emulation on the BF16 tensor cores (gemm_oz)
+  bool oz_faster = false;   // cost model: the emulation beats the FP64 pipe on this list
 };
 
 struct UpLevel {
@@ -52,10 +54,11 @@ struct DownLevel {
 };
 
 enum KClass { K_GEMM = 0, K_GEMM_TC, K_SCHUR, K_SCHUR_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
-              K_OUT, K_NCLASS };
+              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_NCLASS };
 static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "schur_z_dmma",
                                            "schur_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
-                                           "assemble", "add_a", "lesser_fold", "gather", "out"};
+                                           "assemble", "add_a", "lesser_fold", "gather", "out",
+                                           "gemm_z_ozaki", "schur_z_ozaki"};
 
 struct Prof {
   bool on = false;
@@ -77,12 +80,14 @@ struct DeviceState {
   int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
   bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
   bool four_products = false;        // FP64 engine: 4 real products per complex product (else 3M)
+  int fp64_engine = 0;               // 0 cost model, 1 FP64 pipe only, 2 emulation wherever K > 0
   // energy-independent device arrays
   ClusterGlobal* cg = nullptr;
   LevelCluster* lcs = nullptr;
   GJProb* gjp = nullptr;
   GemmProb* gp = nullptr;
   GemmProb* gp128 = nullptr;
+  GemmProb* gpoz = nullptr;
   int32_t *maps = nullptr, *h_rq = nullptr, *own_contact = nullptr;
   int64_t *h_vi = nullptr, *doff = nullptr;
   c64* hval = nullptr;
@@ -93,6 +98,8 @@ struct DeviceState {
   // per-energy strides (elements)
   int64_t aug_es = 0, sq_es = 0, x_es = 0, tt_es = 0, tz_es = 0, tn_es = 0, gjt_es = 0, piv_es = 0;
   int64_t pk_es = 1;                 // tensor-core operand pack buffer (32-bit words per energy)
+  int64_t oz_es = 0;                 // the same for the FP64-emulation slices and scales
+  bool any_oz = false;               // some list runs on the FP64 emulation
   bool use_pack = true;              // HSC_MIXED: pack operands once per launch (else per tile)
   // workspace for `cap` energies
   int64_t cap = 0;
@@ -102,6 +109,7 @@ struct DeviceState {
       *GJT = nullptr;
   int32_t* piv = nullptr;
   uint32_t* PK = nullptr;
+  int64_t pk_cur = 0;                // words per energy of PK (its per-energy stride)
   // host-io staging, requested-pair offsets, batch branch stream
   int64_t io_cap = 0;
   void* io = nullptr;
@@ -151,28 +159,38 @@ cudaError_t upload(DeviceState* d, T** dst, const std::vector<T>& v) {
 
 constexpr int TILE = 64;
 
+// Per-SM cost model of the two FP64-accurate engines in FP64-pipe operations (DFMA equivalents):
+// the FP64 pipe does 3 (4) K DFMA per element of a 64x64 tile; the emulation does, per 128x64 tile
+// and real product, 8 FP64 drains per 128 K values, 36 MMAs of 128x64x16 per 16 K values (about
+// 68 DFMA-times each: ~36 clocks at one MMA-tile per clock, 1.9 DFMA per clock and SM) and the
+// epilogue, plus the slicing pass (about 9 DFMA-times per operand element at HBM speed).
+constexpr double OZ_MMA_DFMA = 68.0, OZ_PACK_DFMA = 9.0;
+
 struct GemmList {
   std::vector<GemmProb>& all;      // 64x64-tile problem lists
   std::vector<GemmProb>& all128;   // 128x128-tile problem lists
-  size_t start, start128;
-  int tiles = 0, tiles128 = 0;
+  std::vector<GemmProb>& alloz;    // 128x64-tile problem lists (FP64 emulation)
+  size_t start, start128, startoz;
+  int tiles = 0, tiles128 = 0, tilesoz = 0;
   int count = 0;
   double flops = 0;
-  int pack_blocks = 0;
-  int64_t pack_words = 0;
-  GemmList(std::vector<GemmProb>& a, std::vector<GemmProb>& b)
-      : all(a), all128(b), start(a.size()), start128(b.size()) {}
+  int pack_blocks = 0, oz_blocks = 0;
+  int64_t pack_words = 0, oz_slices = 0, oz_scales = 0;
+  double cost_z = 0, cost_oz = 0;
+  GemmList(std::vector<GemmProb>& a, std::vector<GemmProb>& b, std::vector<GemmProb>& c)
+      : all(a), all128(b), alloz(c), start(a.size()), start128(b.size()), startoz(c.size()) {}
   void add(int M, int N, int K, int64_t a, int lda, int64_t b, int ldb, int64_t c, int ldc,
            int64_t dd = 0, int ldd = 0, int use_d = 0, int zr0 = 0, int zr1 = 0) {
     if (M <= 0 || N <= 0) return;
-    if (all.size() != start + (size_t)count || all128.size() != start128 + (size_t)count)
+    if (all.size() != start + (size_t)count || all128.size() != start128 + (size_t)count ||
+        alloz.size() != startoz + (size_t)count)
       throw std::logic_error("interleaved GEMM lists");
     ++count;
     GemmProb p{};
     p.M = M; p.N = N; p.K = K;
     p.a = a; p.lda = lda; p.b = b; p.ldb = ldb; p.c = c; p.ldc = ldc; p.d = dd; p.ldd = ldd;
     p.use_d = use_d; p.zr0 = zr0; p.zr1 = zr1;
-    GemmProb q = p;
+    GemmProb q = p, o = p;
     p.tiles_n = (N + TILE - 1) / TILE;
     p.tile_start = tiles;
     tiles += ((M + TILE - 1) / TILE) * p.tiles_n;
@@ -186,9 +204,17 @@ struct GemmList {
     q.pb = pack_words + (int64_t)q.tiles_m * q.ksteps * 8192;
     pack_blocks += (q.tiles_m + q.tiles_n) * q.ksteps;
     pack_words += (int64_t)(q.tiles_m + q.tiles_n) * q.ksteps * 8192;
+    const int t0 = tilesoz;
+    oz_layout(o, oz_blocks, tilesoz, oz_slices, oz_scales);
     flops += 8.0 * M * N * K;
+    const double tz = (double)((M + TILE - 1) / TILE) * p.tiles_n * TILE * TILE;
+    cost_z += tz * 3.0 * K;
+    const double nt = tilesoz - t0;
+    cost_oz += nt * 3.0 * (std::ceil(K / 128.0) * 8 * 8192 + std::ceil(K / 16.0) * 36 * OZ_MMA_DFMA + 4 * 8192) +
+               ((double)M * K + (double)K * N) * OZ_PACK_DFMA;
     all.push_back(p);
     all128.push_back(q);
+    alloz.push_back(o);
   }
   // records the lists; device pointers are patched after upload (index stored in probs)
   GemmPair args(int opa, int opb, double ar, double ai, double br, double bi) const {
@@ -206,9 +232,21 @@ struct GemmList {
     r.tc.total_tiles = tiles128;
     r.tc.pack_blocks = pack_blocks;
     r.tc.pack_words = pack_words;
+    r.oz = g;
+    r.oz.probs = reinterpret_cast<const GemmProb*>(startoz);
+    r.oz.total_tiles = tilesoz;
+    r.oz.pack_blocks = oz_blocks;
+    r.oz.pack_words = oz_slices;
+    r.oz.scale_vals = oz_scales;
+    r.oz_faster = oz_blocks > 0 && cost_oz < 0.7 * cost_z;
     return r;
   }
 };
+
+// words of the pack buffer an emulated list needs per energy: slices, then the scales at the next
+// 16-byte boundary
+int64_t oz_scale_word(const GemmArgs& g) { return ((g.pack_words + 1) / 2 + 3) / 4 * 4; }
+int64_t oz_words(const GemmArgs& g) { return oz_scale_word(g) + 2 * g.scale_vals; }
 
 int build_schedule(hsc_ctx* h) {
   DeviceState* d = h->dev;
@@ -231,7 +269,7 @@ int build_schedule(hsc_ctx* h) {
 
   std::vector<LevelCluster> lcs;
   std::vector<GJProb> gjs;
-  std::vector<GemmProb> gps, gps128;
+  std::vector<GemmProb> gps, gps128, gpsoz;
   int64_t tt_max = 1, tz_max = 1, tn_max = 1, gjt_max = 1;
 
   // leaves: the lesser front is diag(Sigma^<) on the own contact rows and L_iU = 0, so the leaf's
@@ -304,19 +342,19 @@ int build_schedule(hsc_ctx* h) {
     U.nmat = U.nl;
     const LevelCluster* lv = lcs.data() + U.lc;
     {
-      GemmList g1(gps, gps128);
+      GemmList g1(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         g1.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.x, L.m);
       }
       U.u1 = g1.args(OP_N, OP_N, 1, 0, 0, 0);
-      GemmList g2(gps, gps128);
+      GemmList g2(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         g2.add(L.m, L.m, L.n, L.aug + L.n, L.n + L.m, L.x, L.m, L.sq, L.m, L.sq, L.m, 1);
       }
       U.u2 = g2.args(OP_T, OP_N, -1, 0, 1, 0);
-      GemmList g3(gps, gps128);
+      GemmList g3(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
@@ -328,7 +366,7 @@ int build_schedule(hsc_ctx* h) {
           g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.x, L.m, L.tt, L.m, L.aug + L.n, L.n + L.m, 1);
       }
       U.u3 = g3.args(OP_N, OP_C, 0.5, 0, -1, 0);
-      GemmList g4(gps, gps128);
+      GemmList g4(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
         const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
@@ -341,7 +379,7 @@ int build_schedule(hsc_ctx* h) {
       U.u4 = g4.args(OP_T, OP_N, 1, 0, 0, 0);
       const GJProb* gl = gjs.data() + U.gj;
       for (int k0 = 0; k0 < U.max_n; k0 += nb) {
-        GemmList gs(gps, gps128);
+        GemmList gs(gps, gps128, gpsoz);
         for (int k = 0; k < U.nl; ++k) {
           const GJProb& q = gl[k];
           if (q.n <= k0) continue;
@@ -374,19 +412,19 @@ int build_schedule(hsc_ctx* h) {
     tz_max = std::max(tz_max, tz);
     tn_max = std::max(tn_max, tn);
     const LevelCluster* lv = lcs.data() + D.lc;
-    GemmList g1(gps, gps128);
+    GemmList g1(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g1.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m);
     }
     D.d[0] = g1.args(OP_N, OP_N, -1, 0, 0, 0);
-    GemmList g2(gps, gps128);
+    GemmList g2(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g2.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, 1);
     }
     D.d[1] = g2.args(OP_N, OP_T, -1, 0, 1, 0);
-    GemmList g3(gps, gps128);
+    GemmList g3(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
@@ -398,14 +436,14 @@ int build_schedule(hsc_ctx* h) {
         g3.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn + L.n, L.n + L.m);
     }
     D.d[2] = g3.args(OP_N, OP_C, 1, 0, 0, 0);
-    GemmList g4(gps, gps128);
+    GemmList g4(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser && !leafl[ids[k]])   // L_iU = 0 on leaves
         g4.add(L.n, L.m, L.m, L.aug + L.n, L.n + L.m, L.tz, L.m, L.tn + L.n, L.n + L.m, L.tn + L.n, L.n + L.m, 1);
     }
     D.d[3] = g4.args(OP_N, OP_C, 1, 0, 1, 0);
-    GemmList g5(gps, gps128);
+    GemmList g5(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
@@ -417,14 +455,14 @@ int build_schedule(hsc_ctx* h) {
         g5.add(L.n, L.n, L.n, L.aug, L.n + L.m, L.aug, L.n + L.m, L.tn, L.n + L.m);
     }
     D.d[4] = g5.args(OP_N, OP_C, 1, 0, 0, 0);
-    GemmList g6(gps, gps128);
+    GemmList g6(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       if (L.lesser && !leafl[ids[k]])   // L_iU = 0 on leaves
         g6.add(L.n, L.n, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.tn, L.n + L.m, L.tn, L.n + L.m, 1);
     }
     D.d[5] = g6.args(OP_N, OP_H, 1, 0, 1, 0);
-    GemmList g7(gps, gps128);
+    GemmList g7(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
@@ -436,13 +474,13 @@ int build_schedule(hsc_ctx* h) {
         g7.add(L.n, L.n + L.m, L.n, L.aug, L.n + L.m, L.tn, L.n + L.m, L.aug, L.n + L.m);
     }
     D.d[6] = g7.args(OP_N, OP_N, 1, 0, 0, 0);
-    GemmList g8(gps, gps128);
+    GemmList g8(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g8.add(L.n, L.m, L.m, L.x, L.m, L.tz, L.m, L.aug + L.n, L.n + L.m, L.aug + L.n, L.n + L.m, L.lesser);
     }
     D.d[7] = g8.args(OP_N, OP_N, -1, 0, 1, 0);
-    GemmList g9(gps, gps128);
+    GemmList g9(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
       g9.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, L.lesser);
@@ -451,14 +489,25 @@ int build_schedule(hsc_ctx* h) {
   }
   {
     int64_t pk = 1;
-    auto upd = [&](const GemmPair& g) { pk = std::max(pk, g.tc.pack_words); };
+    int64_t oz = 0;
+    d->any_oz = false;
+    auto upd = [&](GemmPair& g) {
+      pk = std::max(pk, g.tc.pack_words);
+      if (d->fp64_engine == 1) g.oz_faster = false;
+      if (d->fp64_engine == 2) g.oz_faster = g.oz.pack_blocks > 0;
+      if (g.oz_faster) {
+        oz = std::max(oz, oz_words(g.oz));
+        d->any_oz = true;
+      }
+    };
     for (auto& U : d->up) {
       upd(U.u1); upd(U.u2); upd(U.u3); upd(U.u4);
       for (auto& st : U.steps) upd(st);
     }
     for (auto& D : d->down)
       for (auto& g : D.d) upd(g);
-    d->pk_es = pk;
+    d->pk_es = (pk + 3) / 4 * 4;
+    d->oz_es = (oz + 3) / 4 * 4;
   }
   d->tt_es = tt_max;
   d->tz_es = tz_max;
@@ -482,6 +531,7 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->gjp, gjs);
   UP(&d->gp, gps);
   UP(&d->gp128, gps128);
+  UP(&d->gpoz, gpsoz);
   UP(&d->maps, P.map_child);
   UP(&d->h_rq, P.h_rq);
   UP(&d->h_vi, P.h_vi);
@@ -500,6 +550,7 @@ int build_schedule(hsc_ctx* h) {
   auto patch = [&](GemmPair& g) {
     g.z.probs = d->gp + reinterpret_cast<size_t>(g.z.probs);
     g.tc.probs = d->gp128 + reinterpret_cast<size_t>(g.tc.probs);
+    g.oz.probs = d->gpoz + reinterpret_cast<size_t>(g.oz.probs);
   };
   for (auto& U : d->up) {
     patch(U.u1); patch(U.u2); patch(U.u3); patch(U.u4);
@@ -511,17 +562,25 @@ int build_schedule(hsc_ctx* h) {
   return HSC_OK;
 }
 
-int64_t bytes_per_energy(const DeviceState* d, bool pack = false) {
-  int64_t c = 4 * d->aug_es + 2 * d->sq_es + d->x_es + d->tt_es + 3 * d->tz_es + d->tn_es + d->gjt_es;
-  return c * (int64_t)sizeof(c64) + d->piv_es * 4 + (pack ? d->pk_es * 4 : 0);
+// pack-buffer words per energy a solve in this precision needs (0: no pack buffer)
+int64_t pack_words_needed(const DeviceState* d, int precision) {
+  int64_t w = d->any_oz ? d->oz_es : 0;   // the emulation runs in both precisions (FP64 levels)
+  if (precision == HSC_MIXED && d->use_pack) w = std::max(w, d->pk_es);
+  return w;
 }
 
-int ensure_arena(hsc_ctx* h, int64_t want, bool pack) {
+int64_t bytes_per_energy(const DeviceState* d, int64_t pack_words = 0) {
+  int64_t c = 4 * d->aug_es + 2 * d->sq_es + d->x_es + d->tt_es + 3 * d->tz_es + d->tn_es + d->gjt_es;
+  return c * (int64_t)sizeof(c64) + d->piv_es * 4 + pack_words * 4;
+}
+
+int ensure_arena(hsc_ctx* h, int64_t want, int64_t pack_words) {
   DeviceState* d = h->dev;
-  if (d->cap >= want && (!pack || d->PK)) return HSC_OK;
+  if (d->cap >= want && d->pk_cur >= pack_words) return HSC_OK;
   want = std::max(want, d->cap);
-  if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->cap = 0; }
-  size_t bytes = (size_t)bytes_per_energy(d, pack) * want + 64 * 256;
+  pack_words = std::max(pack_words, d->pk_cur);
+  if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->cap = 0; d->pk_cur = 0; d->PK = nullptr; }
+  size_t bytes = (size_t)bytes_per_energy(d, pack_words) * want + 64 * 256;
   cudaError_t e = cudaMalloc(&d->arena, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -547,7 +606,8 @@ int ensure_arena(hsc_ctx* h, int64_t want, bool pack) {
   d->N = (c64*)take(d->tn_es, 16);
   d->GJT = (c64*)take(d->gjt_es, 16);
   d->piv = (int32_t*)take(d->piv_es, 4);
-  d->PK = pack ? (uint32_t*)take(d->pk_es, 4) : nullptr;
+  d->PK = pack_words > 0 ? (uint32_t*)take(pack_words, 4) : nullptr;
+  d->pk_cur = pack_words;
   d->cap = want;
   return HSC_OK;
 }
@@ -601,19 +661,24 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
   // ---- upward (Algorithm 1 first loop, Algorithm 2 fold) ----
   bool tc = false;   // current level's GEMMs on the tensor cores (mixed mode, below the top levels)
   bool schur = false;   // the launch is Algorithm 1's Schur update (profiled separately)
-  auto gemm = [&](const GemmArgs& gz, const GemmArgs& gt) -> int {
+  auto gemm = [&](const GemmPair& pr, const GemmArgs& gz, const GemmArgs& gt, const GemmArgs& go) -> int {
     if (gz.total_tiles <= 0) return HSC_OK;
-    if (tc && d->PK)
+    if (tc && d->PK && d->use_pack)
       LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 2, gt.flops * ne, 0.0,
-             gemm_tc_packed(gt, ne, d->PK, d->pk_es, d->flag + 2, s));
+             gemm_tc_packed(gt, ne, d->PK, d->pk_cur, d->flag + 2, s));
     else if (tc) LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
+    else if (pr.oz_faster && d->PK && oz_words(go) <= d->pk_cur)
+      LAUNCH(schur ? K_SCHUR_OZ : K_GEMM_OZ, 2, go.flops * ne, 0.0,
+             gemm_oz(go, ne, reinterpret_cast<uint16_t*>(d->PK), 2 * d->pk_cur,
+                     reinterpret_cast<double*>(d->PK + oz_scale_word(go)), d->pk_cur / 2, d->flag + 2, s));
     else LAUNCH(schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s, d->four_products));
     return HSC_OK;
   };
-#define GEMM(pair, ...)                                                   \
-  do {                                                                    \
-    int _r = gemm(bind((pair).z, __VA_ARGS__), bind((pair).tc, __VA_ARGS__)); \
-    if (_r != HSC_OK) return _r;                                          \
+#define GEMM(pair, ...)                                                                          \
+  do {                                                                                           \
+    int _r = gemm((pair), bind((pair).z, __VA_ARGS__), bind((pair).tc, __VA_ARGS__),             \
+                  bind((pair).oz, __VA_ARGS__));                                                 \
+    if (_r != HSC_OK) return _r;                                                                 \
   } while (0)
   const int nup = (int)d->up.size();
   for (int hl = 0; hl < nup; ++hl) {
@@ -741,18 +806,27 @@ using namespace hsc;
 namespace hsc {
 namespace {
 
+// Creates the handle's device state on the current device with the handle's options (no schedule).
+int new_state(hsc_ctx* h) {
+  h->dev = new DeviceState();
+  CK(cudaGetDevice(&h->dev->device));
+  h->dev->nb = h->opt_nb;
+  h->dev->fp64_levels = h->opt_fp64_levels;
+  h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
+  h->dev->four_products = h->opt_4m != 0;
+  h->dev->fp64_engine = h->opt_fp64_engine;
+  if (const char* v = getenv("HSC_FP64_ENGINE")) h->dev->fp64_engine = atoi(v);
+  if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
+  if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
+  if (const char* v = getenv("HSC_TC_PACK")) h->dev->use_pack = atoi(v) != 0;
+  return HSC_OK;
+}
+
 // Creates the device state (applying the handle's options) and the device schedule.
 int get_state(hsc_ctx* h) {
   if (!h->dev) {
-    h->dev = new DeviceState();
-    CK(cudaGetDevice(&h->dev->device));
-    h->dev->nb = h->opt_nb;
-    h->dev->fp64_levels = h->opt_fp64_levels;
-    h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
-    h->dev->four_products = h->opt_4m != 0;
-    if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
-    if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
-    if (const char* v = getenv("HSC_TC_PACK")) h->dev->use_pack = atoi(v) != 0;
+    int rc = new_state(h);
+    if (rc != HSC_OK) return rc;
   }
   DeviceState* d = h->dev;
   int cur = 0;
@@ -815,9 +889,9 @@ int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
 }
 
 // Sizes (and allocates) the workspace for waves of at most `wave` energies.
-int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out, bool pack) {
+int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out, int precision) {
   DeviceState* d = h->dev;
-  pack = pack && d->use_pack;
+  const int64_t pack = pack_words_needed(d, precision);
   const int64_t per = bytes_per_energy(d, pack);
   int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(byte_cap / per, 0));
   if (d->cap > 0) wave = std::max<int64_t>(std::min<int64_t>(n_E, d->cap), wave);
@@ -876,7 +950,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
   if ((rc = upload_pairs(h, n_req, req_pairs)) != HSC_OK) return rc;
   DeviceState* d = h->dev;
   int64_t wave = 0;
-  if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave, precision == HSC_MIXED)) != HSC_OK) return rc;
+  if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave, precision)) != HSC_OK) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (io_on_device) {
     rc = enqueue_device(h, n_E, wave, E, eta, sigma_r, sigma_less, precision, n_req, diag_gr, diag_gl,
@@ -964,9 +1038,9 @@ extern "C" int hsc_debug_blocks(hsc_t h, int32_t which, int32_t energy, hsc_c128
 
 extern "C" int hsc_profile(hsc_t h, int32_t enable) {
   if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
-  if (!h->dev) {
-    h->dev = new DeviceState();
-    CK(cudaGetDevice(&h->dev->device));
+  if (!h->dev) {   // the options set on the handle must reach the state a later solve uses
+    int rc = new_state(h);
+    if (rc != HSC_OK) return rc;
   }
   Prof& p = h->dev->prof;
   p.on = enable != 0;
@@ -1008,7 +1082,7 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
                               const hsc_c128* A, int32_t lda, const hsc_c128* B, int32_t ldb,
                               hsc_c128* C, int32_t ldc, const hsc_c128* D, int32_t ldd,
                               double ar, double ai, double br, double bi, void* stream) {
-  if (M < 0 || N < 0 || K < 0 || opa < 0 || opa > 3 || opb < 0 || opb > 3)
+  if (M < 0 || N < 0 || K < 0 || opa < 0 || opa > 3 || opb < 0 || opb > 3 || engine < 0 || engine > 4)
     return hsc_fail(nullptr, HSC_ERR_ARG, "bad GEMM arguments");
   GemmProb p{};
   p.M = M; p.N = N; p.K = K;
@@ -1022,7 +1096,7 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   p.pack_start = 0;
   p.pa = 0;
   p.pb = (int64_t)p.tiles_m * p.ksteps * 8192;
-  const int64_t pack_words = (int64_t)(p.tiles_m + p.tiles_n) * p.ksteps * 8192;
+  int64_t pack_words = (int64_t)(p.tiles_m + p.tiles_n) * p.ksteps * 8192;
   GemmProb* dp = nullptr;
   int* flag = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1037,12 +1111,27 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   g.pack_blocks = (p.tiles_m + p.tiles_n) * p.ksteps;
   g.pack_words = pack_words;
   uint32_t* pk = nullptr;
-  if (engine == 2 && cudaMalloc(&pk, std::max<int64_t>(pack_words, 1) * 4) != cudaSuccess) {
+  int64_t oz_slices = 0, oz_scales = 0;
+  if (engine == 4) {   // FP64 emulation on the BF16 tensor cores: its own tiling and pack layout
+    int blocks = 0, tiles = 0;
+    oz_layout(p, blocks, tiles, oz_slices, oz_scales);
+    cudaMemcpy(dp, &p, sizeof(p), cudaMemcpyHostToDevice);
+    g.total_tiles = tiles;
+    g.pack_blocks = blocks;
+    g.pack_words = oz_slices;
+    g.scale_vals = oz_scales;
+    pack_words = (oz_slices + 1) / 2 + 2 * oz_scales + 4;
+  }
+  if ((engine == 2 || engine == 4) && cudaMalloc(&pk, std::max<int64_t>(pack_words, 1) * 4) != cudaSuccess) {
     cudaFree(dp);
     cudaFree(flag);
     return hsc_fail(nullptr, HSC_ERR_OOM, "cudaMalloc pack");
   }
-  cudaError_t e = engine == 2 ? gemm_tc_packed(g, 1, pk, pack_words, flag, s)
+  // engine 4: slices first, then the scales at the next 16-byte boundary
+  const int64_t oz_sc_words = ((oz_slices + 1) / 2 + 3) / 4 * 4;
+  cudaError_t e = engine == 4 ? gemm_oz(g, 1, reinterpret_cast<uint16_t*>(pk), oz_slices,
+                                        reinterpret_cast<double*>(pk + oz_sc_words), oz_scales, flag, s)
+                  : engine == 2 ? gemm_tc_packed(g, 1, pk, pack_words, flag, s)
                   : engine == 1 ? gemm_tc(g, 1, flag, s) : gemm_z(g, 1, s, engine == 3);
   int hf = 0;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1093,7 +1182,7 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
     if (rc == HSC_OK) rc = get_state(h);
     if (rc == HSC_OK) rc = upload_pairs(h, it.n_req, it.req_pairs);
     if (rc != HSC_OK) return item_fail(i, h, rc);
-    need[i] = (double)bytes_per_energy(h->dev, precision == HSC_MIXED && h->dev->use_pack) *
+    need[i] = (double)bytes_per_energy(h->dev, pack_words_needed(h->dev, precision)) *
               (double)std::max<int64_t>(it.n_E, 1);
     need_total += need[i];
   }
@@ -1102,7 +1191,7 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
   for (int i = 0; i < n_items; ++i) {
     hsc_ctx* h = items[i].h;
     int64_t cap = (int64_t)(budget * need[i] / need_total);
-    int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i], precision == HSC_MIXED);
+    int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i], precision);
     if (rc != HSC_OK) return item_fail(i, h, rc);
     if (!h->dev->branch) {
       cudaError_t e = cudaStreamCreateWithFlags(&h->dev->branch, cudaStreamNonBlocking);

@@ -23,6 +23,7 @@ EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_b
            "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
            "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF, HSC_OPT_COMPLEX_4M = 1, 2, 3, 4, 5
+HSC_OPT_FP64_ENGINE = 6
 
 
 class hsc_tree_stats(ctypes.Structure):

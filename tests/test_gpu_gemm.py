@@ -1,5 +1,6 @@
-"""Both GEMM engines of the solve (FP64 tensor pipe; tcgen05 3xTF32) against numpy complex128, on
-ragged shapes spanning several tiles and every operand-op combination the solve uses."""
+"""The GEMM engines of the solve (FP64 tensor pipe; FP64 emulation on the BF16 tensor cores;
+tcgen05 3xTF32) against numpy complex128, on ragged shapes spanning several tiles and every
+operand-op combination the solve uses."""
 import ctypes
 
 import numpy as np
@@ -84,3 +85,73 @@ def test_tcgen05_3xtf32_engine(lib, oa, ob, M, N, K):
     significant bits; FP32 accumulation adds ~K * 2^-24."""
     err = run(lib, 1, oa, ob, M, N, K, M + N + K)
     assert err <= 2e-6, err
+
+
+@pytest.mark.parametrize("oa,ob", OPS)
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_fp64_emulation_engine(lib, oa, ob, M, N, K):
+    """Eight slices of 7 bits on the BF16 tensor cores: per K value the error is below
+    2^-52.8 sigma tau (power-of-two row and column scales), so at FP64 level of |A||B|."""
+    err = run(lib, 4, oa, ob, M, N, K, M + N + K)
+    assert err <= 1e-13, err
+
+
+def _emulated(L, A, B, oa=0, ob=0):
+    import torch
+    M, K = A.shape if oa == 0 else A.shape[::-1]
+    N = B.shape[1] if ob == 0 else B.shape[0]
+    dv = torch.device("cuda")
+    tA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.complex128).view(np.float64)).to(dv)
+    tB = torch.from_numpy(np.ascontiguousarray(B, dtype=np.complex128).view(np.float64)).to(dv)
+    tC = torch.full((M, 2 * N), float("nan"), dtype=torch.float64, device=dv)
+    code = L.hsc_debug_gemm(4, oa, ob, M, N, K, tA.data_ptr(), A.shape[1], tB.data_ptr(), B.shape[1],
+                            tC.data_ptr(), N, None, 0, 1.0, 0.0, 0.0, 0.0, None)
+    assert code == 0, hsc.hsc_last_error()
+    return tC.cpu().numpy().view(np.complex128)
+
+
+@pytest.mark.parametrize("K", [1, 128, 517, 2048])
+def test_fp64_emulation_exact_on_short_integers(lib, K):
+    """Entries with at most 5 significant bits fit the first slice: the product is then computed
+    exactly (integer slice products, FP32 accumulation exact below 2^24), equal to numpy's."""
+    rng = np.random.default_rng(K)
+    A = rng.integers(-15, 16, (70, K)) + 1j * rng.integers(-15, 16, (70, K))
+    B = rng.integers(-15, 16, (K, 90)) + 1j * rng.integers(-15, 16, (K, 90))
+    C = _emulated(lib, A, B)
+    assert np.array_equal(C, A @ B)
+
+
+@pytest.mark.parametrize("K", [128, 200, 1000])
+def test_fp64_emulation_full_slices(lib, K):
+    """x = 1 - 2^-53 (the largest double below 1) makes slices 1-7 equal to 127 and slice 8 equal to
+    120: the largest FP32 partial sums the accumulation meets (8 pairs on diagonal 9, 16.3e6 over
+    128 K values, below 2^24). The result must be K times the kept diagonals (s + r <= 9) up to the
+    FP64 rounding of the drain; a lost unit in the accumulator of diagonal d would add
+    2^(-7 d) per chunk."""
+    from fractions import Fraction
+    x = 1.0 - 2.0 ** -53
+    t = [127] * 7 + [120]
+    assert sum(Fraction(t[s - 1], 2 ** (7 * s)) for s in range(1, 9)) == Fraction(x)
+    pairs = [(s, r) for s in range(1, 9) for r in range(1, 9)]
+    term = lambda s, r: Fraction(t[s - 1] * t[r - 1], 2 ** (7 * (s + r)))
+    kept = sum(term(s, r) for s, r in pairs if s + r <= 9)
+    dropped = sum(term(s, r) for s, r in pairs if s + r >= 10)
+    assert kept + dropped == Fraction(x) ** 2
+    A = np.full((130, K), x, dtype=np.complex128)
+    B = np.full((K, 70), x, dtype=np.complex128)
+    C = _emulated(lib, A, B)
+    assert np.all(C.imag == 0.0)
+    assert np.max(np.abs(C.real - float(K * kept))) <= K * 2.0 ** -50
+
+
+def test_fp64_emulation_row_scaling(lib):
+    """Rows of A and columns of B spanning 2^-300 .. 2^300: each gets its own power-of-two scale,
+    so the error stays relative to the row and column maxima."""
+    rng = np.random.default_rng(7)
+    M, N, K = 96, 80, 300
+    A = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * 2.0 ** rng.integers(-300, 300, (M, 1))
+    B = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * 2.0 ** rng.integers(-300, 300, (1, N))
+    C = _emulated(lib, A, B)
+    ref = A @ B
+    bound = K * np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :] * 2.0 ** -46
+    assert np.all(np.abs(C - ref) <= bound)

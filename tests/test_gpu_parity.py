@@ -41,10 +41,18 @@ def _gpu():
     hsc.load()
 
 
-def _dense_case(dev, leaf, energies, eta=ETA_WELL, f=(1.0, 0.0), pairs=None, tol=TOL):
+def _dense_case(dev, leaf, energies, eta=ETA_WELL, f=(1.0, 0.0), pairs=None, tol=TOL, engine=None):
     sr, sl = W.self_energies(dev, len(energies), f)
     s = hsc.Solver(dev, leaf)
+    if engine is not None:
+        hsc.hsc_set_option(s.h, hsc.HSC_OPT_FP64_ENGINE, engine)
+        hsc.hsc_profile(s.h, True)
     dgr, dgl, pgr, pgl = s.solve(energies, eta, sr, sl, pairs=pairs)
+    if engine is not None:
+        launches = {p["name"]: p["launches"] for p in hsc.hsc_profile_read(s.h)}
+        emulated = launches.get("gemm_z_ozaki", 0) + launches.get("schur_z_ozaki", 0)
+        # engine 2 runs every product list with K > 0 on the emulation, engine 1 none
+        assert (emulated > 0) == (engine == 2), launches
     Hd = dev.to_scipy().toarray()
     for k, E in enumerate(energies):
         G, Gl = dense.solve(Hd, E, eta, dev.contact_unknowns(), sr[k], sl[k])
@@ -275,3 +283,39 @@ def test_resonant_case_three_versus_four_products():
         errs[four] = max(relerr(dgr[0], np.diag(G)), relerr(dgl[0], np.diag(Gl)))
     print(f"resonant 9x4x4: 3 products {errs[0]:.2e}, 4 products {errs[1]:.2e}")
     assert errs[1] <= 1e-5 and errs[0] <= TOL_RESONANT
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_fp64_engines_against_dense(engine):
+    """Both FP64-accurate engines of the block products: the FP64 pipe (engine 1) and the FP64
+    emulation on the BF16 tensor cores (engine 2, eight exact 7-bit slices per operand) must meet
+    TOL on the tiny cube, a ragged grid, the multi-orbital wire and the degenerate chain, and
+    TOL_RESONANT at eta = 1e-6."""
+    cfg = W.tiny()
+    _dense_case(cfg["dev"], cfg["leaf"], cfg["energies"], cfg["eta"], cfg["f"],
+                pairs=W.plane_pairs(cfg["dev"], 3), engine=engine)
+    dev = W.cubic_device((7, 5, 6), W=1.0, seed=18)
+    E = np.array([-2.9, -0.4, 0.0, 0.23, 1.3, 3.7])
+    _dense_case(dev, 2, E, f=(1.0, 0.3), pairs=W.plane_pairs(dev, 3), engine=engine)
+    _dense_case(dev, 2, E, eta=1e-6, f=(1.0, 0.3), tol=TOL_RESONANT, engine=engine)
+    wire = W.wire_device((6, 3, 2), orb=2, seed=5)
+    _dense_case(wire, 3, np.array([-1.1, 0.4]), f=(1.0, 0.5), engine=engine)
+    chain = W.chain_device(40, eps=np.linspace(-0.5, 0.5, 40))
+    _dense_case(chain, 2, np.array([0.1, 0.9]), f=(0.2, 1.0), engine=engine)
+
+
+def test_emulated_and_fp64_pipe_agree_on_mid_cube():
+    """12^3 cube, leaves <= 4, 4 energies: the emulated and FP64-pipe solves agree to 1e-11 (both
+    within rounding of the same block steps at eta = 0.05)."""
+    dev = W.cubic_device((12, 12, 12), W=1.0, seed=3)
+    E = np.array([-1.7, -0.2, 0.45, 2.2])
+    sr, sl = W.self_energies(dev, len(E), (1.0, 0.0))
+    out = {}
+    for engine in (1, 2):
+        s = hsc.Solver(dev, 4)
+        hsc.hsc_set_option(s.h, hsc.HSC_OPT_FP64_ENGINE, engine)
+        out[engine] = s.solve(E, ETA_WELL, sr, sl)
+        s.close()
+    for k in range(len(E)):
+        assert relerr(out[2][0][k], out[1][0][k]) <= 1e-11
+        assert relerr(out[2][1][k], out[1][1][k]) <= 1e-11
