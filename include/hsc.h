@@ -136,13 +136,25 @@ typedef enum {
   HSC_OPT_COMPLEX_4M = 5,     /* FP64 block products with 4 real products per complex product   */
                               /* (default 0: 3 products, Im = (Ar+Ai)(Br+Bi) - ArBr - AiBi, 25 % */
                               /* less FP64-pipe work, slightly larger rounding constant)        */
-  HSC_OPT_FP64_ENGINE = 6     /* engine of the FP64-accurate block products: 0 (default) picks  */
+  HSC_OPT_FP64_ENGINE = 6,    /* engine of the FP64-accurate block products: 0 (default) picks  */
                               /* per product list by a cost model, 1 = FP64 pipe only, 2 = FP64 */
                               /* emulation on the BF16 tensor cores wherever K > 0. The         */
                               /* emulation splits each real operand exactly into eight 7-bit    */
                               /* slices (power-of-two row / column scales) and accumulates the  */
                               /* slice products exactly; its error per K value is below         */
                               /* 2^-52.8 times the two scales, at the level of FP64 rounding.   */
+  HSC_OPT_RESOLVE_DIGITS = 7, /* d > 0: hsc_solve solves every energy whose residual (see      */
+                              /* hsc_residual) exceeds 10^-d again on the alternate separator   */
+                              /* trees in turn (the root plane kept, every deeper cut moved by  */
+                              /* +1, -1, +2, -2 planes; an energy goes to the next tree while   */
+                              /* still above the threshold) and keeps, per energy, the result   */
+                              /* with the smallest residual; 0 = off; default 4. HSC_FP64 solves */
+                              /* only (a mixed-precision residual reflects its FP32 rounding).  */
+                              /* Each alternate tree is analysed on first need and works in the */
+                              /* handle's own workspace after the first pass.                   */
+                              /* hsc_solve_batch does not re-solve.                             */
+  HSC_OPT_TREE_VARIANT = 8    /* 1..4: the next hsc_analyze builds that alternate separator     */
+                              /* tree itself (0, default: the plain tree)                       */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);
@@ -211,6 +223,23 @@ typedef struct {
   double flops;
   double bytes;
 } hsc_kernel_stat;
+
+/* hsc_residual -- a-posteriori check of the last solve on this handle: out[k] = max over unknowns u
+ *   of |Re r_u| + |Im r_u|, r_u = (A G^r - I)_uu at energy k, evaluated from the computed blocks
+ *   (every non-zero A_uv joins unknowns whose G^r entry is stored, G^r = (G^r)^T). A relative error
+ *   x in the diagonal and pattern entries of G^r shows up as about |A| |G| x. Host array of
+ *   n_E <= the last solve's n_E; synchronises the device. Errors: HSC_ERR_ARG, HSC_ERR_STATE,
+ *   HSC_ERR_CUDA. */
+int hsc_residual(hsc_t h, int64_t n_E, double* out);
+
+/* hsc_growth -- element growth of the last solve on this handle: out[k] = max over the cluster
+ *   blocks of Algorithm 1 of the largest |Re| + |Im| entry of D_i^{-1} at energy k (in 1/eV). The
+ *   elimination order is fixed by the separator tree and pivots only inside a cluster block, so a
+ *   cluster whose isolated levels lie within ~eta of E makes this large, and the downward pass
+ *   (Eq. 4) then subtracts terms of that size from each other: the results lose digits in
+ *   proportion. out: host array of n_E <= the last solve's n_E. Synchronises the device.
+ *   Errors: HSC_ERR_ARG, HSC_ERR_STATE (no such solve), HSC_ERR_CUDA. */
+int hsc_growth(hsc_t h, int64_t n_E, double* out);
 
 /* hsc_profile -- reset the kernel statistics; enable = 1 additionally brackets every kernel launch
  *   of subsequent hsc_solve calls with CUDA events on the solve's stream (device-side timing;

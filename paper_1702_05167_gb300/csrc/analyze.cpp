@@ -33,8 +33,11 @@ struct Builder {
   }
 
   // Geometric nested dissection of the box [lo, hi] (inclusive): cut the longest extent (ties in
-  // x, y, z order) by the plane at floor((lo+hi)/2); stop when every extent is <= leaf.
-  int box(int lo[3], int hi[3]) {
+  // x, y, z order) by the plane at floor((lo+hi)/2); stop when every extent is <= leaf. The
+  // alternate trees keep the root plane and move every deeper cut by +1, -1, +2 or -2 planes
+  // (in.variant = 1..4) where both halves stay non-empty, so their boxes (and isolated spectra)
+  // differ.
+  int box(int lo[3], int hi[3], int depth = 0) {
     int ext[3];
     for (int d = 0; d < 3; ++d) {
       ext[d] = hi[d] - lo[d] + 1;
@@ -53,19 +56,25 @@ struct Builder {
     for (int k = 1; k < 3; ++k)
       if (ext[k] > ext[d]) d = k;
     int mid = (lo[d] + hi[d]) / 2;
+    if (depth > 0 && in.variant > 0) {
+      static const int kShift[5] = {0, 1, -1, 2, -2};
+      const int m2 = mid + kShift[in.variant];
+      if (m2 > lo[d] && m2 < hi[d]) mid = m2;
+    }
     int llo[3] = {lo[0], lo[1], lo[2]}, lhi[3] = {hi[0], hi[1], hi[2]};
     int rlo[3] = {lo[0], lo[1], lo[2]}, rhi[3] = {hi[0], hi[1], hi[2]};
     lhi[d] = mid - 1;
     rlo[d] = mid + 1;
-    int c0 = box(llo, lhi);
-    int c1 = box(rlo, rhi);
+    int c0 = box(llo, lhi, depth + 1);
+    int c1 = box(rlo, rhi, depth + 1);
     int slo[3] = {lo[0], lo[1], lo[2]}, shi[3] = {hi[0], hi[1], hi[2]};
     slo[d] = shi[d] = mid;
     return make(sites_in(slo, shi), c0, c1);
   }
 
   // General-graph bisection: breadth-first level sets from a pseudo-peripheral site; the level
-  // where the running count crosses half the set is the separator.
+  // where the running count crosses half the set is the separator (below the root, the alternate
+  // trees move it by +1, -1, +2 or -2 levels (variant 1..4) where both sides stay non-empty).
   int graph(std::vector<int> S, std::vector<int>& mark, int tag) {
     if (S.empty()) return -1;
     const int64_t lim = (int64_t)leaf * leaf * leaf;
@@ -105,6 +114,11 @@ struct Builder {
       if (2 * run >= (int64_t)S.size()) { cut = l; break; }
     }
     if (cut == 0) cut = std::min(1, maxl);
+    if (tag > 0 && in.variant > 0) {
+      static const int kShift[5] = {0, 1, -1, 2, -2};
+      const int c2 = cut + kShift[in.variant];
+      if (c2 >= 1 && c2 < maxl) cut = c2;
+    }
     for (int s : S) {
       if (lev[s] < 0) right.push_back(s);
       else if (lev[s] < cut) left.push_back(s);

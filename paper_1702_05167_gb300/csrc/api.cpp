@@ -115,6 +115,8 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   in.contact_ptr = h->contact_ptr.data();
   in.contact_sites = h->contact_sites.data();
   std::memcpy(in.dims, h->dims, sizeof(in.dims));
+  in.variant = h->nd_variant;
+  hsc_drop_alt(h);   // the twin follows the leaf size of this analysis
   std::string e;
   try {
     e = hsc::analyze(in, leaf_max, h->plan);
@@ -192,11 +194,20 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       if (value < 0 || value > 2) return hsc_fail(h, HSC_ERR_ARG, "engine must be 0, 1 or 2");
       h->opt_fp64_engine = value;
       break;
+    case HSC_OPT_RESOLVE_DIGITS:
+      if (value < 0 || value > 15) return hsc_fail(h, HSC_ERR_ARG, "residual digits must be in [0, 15]");
+      h->opt_resolve = value;
+      break;
+    case HSC_OPT_TREE_VARIANT:
+      if (value < 0 || value > 4 || h->is_alt) return hsc_fail(h, HSC_ERR_ARG, "tree variant must be in [0, 4]");
+      h->nd_variant = value;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   hsc::device_state_free(h->dev);   // schedules depend on the options
   h->dev = nullptr;
+  hsc_drop_alt(h);
   return HSC_OK;
 }
 
@@ -209,6 +220,8 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_LEAF: *value = h->leaf_max; break;
     case HSC_OPT_COMPLEX_4M: *value = h->opt_4m; break;
     case HSC_OPT_FP64_ENGINE: *value = h->opt_fp64_engine; break;
+    case HSC_OPT_RESOLVE_DIGITS: *value = h->opt_resolve; break;
+    case HSC_OPT_TREE_VARIANT: *value = h->nd_variant; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   return HSC_OK;
@@ -216,9 +229,50 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
 
 extern "C" const char* hsc_last_error(hsc_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
+void hsc_drop_alt(hsc_ctx* h) {
+  for (hsc_ctx*& a : h->alt) {
+    if (!a) continue;
+    hsc::device_state_free(a->dev);
+    delete a;
+    a = nullptr;
+  }
+}
+
+hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
+  if (v < 1 || v > 4) return nullptr;
+  if (h->alt[v - 1]) return h->alt[v - 1];
+  if (!h->analyzed || h->is_alt || v == h->nd_variant) return nullptr;
+  hsc_ctx* a = new (std::nothrow) hsc_ctx();
+  if (!a) return nullptr;
+  a->n = h->n;
+  a->orb = h->orb;
+  a->rowptr = h->rowptr;
+  a->col = h->col;
+  a->val = h->val;
+  a->n_contacts = h->n_contacts;
+  a->contact_ptr = h->contact_ptr;
+  a->contact_sites = h->contact_sites;
+  a->n_contact_unknowns = h->n_contact_unknowns;
+  std::memcpy(a->dims, h->dims, sizeof(a->dims));
+  a->opt_nb = h->opt_nb;
+  a->opt_fp64_levels = h->opt_fp64_levels;
+  a->opt_gj_fp64 = h->opt_gj_fp64;
+  a->opt_4m = h->opt_4m;
+  a->opt_fp64_engine = h->opt_fp64_engine;
+  a->nd_variant = v;
+  a->is_alt = true;
+  if (hsc_analyze(a, h->leaf_max, nullptr) != HSC_OK) {
+    delete a;
+    return nullptr;
+  }
+  h->alt[v - 1] = a;
+  return a;
+}
+
 extern "C" int hsc_destroy(hsc_t h) {
   if (!h) return HSC_OK;
   hsc::device_state_free(h->dev);
+  hsc_drop_alt(h);
   delete h;
   return HSC_OK;
 }

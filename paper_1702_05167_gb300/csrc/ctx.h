@@ -33,7 +33,16 @@ struct hsc_ctx {
   int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe
   int opt_4m = 0;             // FP64 engine: 4 real products per complex product (default 3)
   int opt_fp64_engine = 0;    // FP64-accurate products: 0 cost model, 1 FP64 pipe, 2 emulation
+  int opt_resolve = 4;        // d: re-solve energies whose residual exceeds 10^-d (0: off)
   int leaf_max = 0;           // last hsc_analyze leaf size
+  // alternate separator trees 1..4 (cuts below the root shifted), built on first need by hsc_solve
+  int nd_variant = 0;
+  bool is_alt = false;
+  hsc_ctx* alt[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 int hsc_fail(hsc_ctx* h, int code, const std::string& msg);
+// The alternate-tree twin of h for variant v (1..4): same matrix, contacts and options, analysed
+// at h's leaf size; created on first call; nullptr if it cannot be built.
+hsc_ctx* hsc_alt(hsc_ctx* h, int v);
+void hsc_drop_alt(hsc_ctx* h);

@@ -227,8 +227,9 @@ __global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32
 }
 
 // undo the row interchanges on the columns of the in-place inverse: A^{-1} = Y P
+// Also records the growth of the energy: the largest |Re| + |Im| of any entry of D_i^{-1}.
 __global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const int32_t* piv,
-                             int64_t piv_es) {
+                             int64_t piv_es, float* growth) {
   extern __shared__ unsigned char smem[];
   const GJProb P = probs[blockIdx.x];
   const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
@@ -244,13 +245,50 @@ __global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const in
       if (p != j) { int t = idx[j]; idx[j] = idx[p]; idx[p] = t; }
     }
   __syncthreads();
+  double mx = 0.0;
   for (int r = 0; r < n; ++r) {
     c64* row = A + (int64_t)r * ld;
-    for (int c = tid; c < n; c += blockDim.x) buf[c] = row[c];
+    for (int c = tid; c < n; c += blockDim.x) {
+      buf[c] = row[c];
+      mx = fmax(mx, fabs(buf[c].x) + fabs(buf[c].y));
+    }
     __syncthreads();
     for (int c = tid; c < n; c += blockDim.x) row[c] = buf[idx[c]];
     __syncthreads();
   }
+  if (growth) {
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // positive floats order as their bit patterns; NaN or overflow records +inf
+    const float f = (mx == mx && mx < 3.0e38) ? (float)mx : __int_as_float(0x7f800000);
+    if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(growth + e), __float_as_uint(f));
+  }
+}
+
+// ---- a-posteriori check: diagonal residual of A G^r = I ---------------------------------------
+// Every non-zero A_uv joins two unknowns whose G^r entry lies in a stored block (same cluster, or
+// one in the other's update set; G^r = (G^r)^T for the complex-symmetric A of Eq. 1), so
+//   r_u = (E + i eta - Sigma^r_u) G_uu - sum_v H_uv G_uv - 1
+// is computable from the solve's own output; the energy's record is max_u |Re r_u| + |Im r_u|.
+__global__ void k_residual(int64_t n, const int64_t* rowptr, const c64* hval, const int64_t* loc,
+                           const int64_t* doff, const int32_t* unk_slot, const double* E, double eta,
+                           const c64* sr, int64_t ncs, const c64* G, int64_t aug_es, float* resid) {
+  const int e = blockIdx.y;
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (u < n) {
+    const c64* Ge = G + e * aug_es;
+    c64 a = make_double2(E[e], eta);
+    const int slot = unk_slot[u];
+    if (slot >= 0) a = csub(a, sr[e * ncs + slot]);
+    c64 r = cmul(a, Ge[doff[u]]);
+    r.x -= 1.0;
+    for (int64_t k = rowptr[u]; k < rowptr[u + 1]; ++k) r = csub(r, cmul(hval[k], Ge[loc[k]]));
+    mx = fabs(r.x) + fabs(r.y);
+    if (!(mx == mx)) mx = 3.0e38;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float f = mx < 3.0e38 ? (float)mx : __int_as_float(0x7f800000);
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(resid + e), __float_as_uint(f));
 }
 
 // ---- lesser fold completion: LS += Z - Z^dagger --------------------------------------------
@@ -406,6 +444,16 @@ cudaError_t launch_add_a(const LevelCluster* lc, int nl, int64_t max_h, int max_
   return cudaGetLastError();
 }
 
+cudaError_t launch_residual(int64_t n, const int64_t* rowptr, const c64* hval, const int64_t* loc,
+                           const int64_t* doff, const int32_t* unk_slot, const double* E, double eta,
+                           const c64* sr, int64_t ncs, const c64* G, int64_t aug_es, float* resid,
+                           int ne, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_residual<<<dim3((unsigned)((n + 255) / 256), ne), 256, 0, s>>>(n, rowptr, hval, loc, doff, unk_slot, E, eta,
+                                                                   sr, ncs, G, aug_es, resid);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es, int32_t* piv,
                             int64_t piv_es, c64* Mt, c64* Rt, int64_t t_es, int k0, int nb, int ne,
                             int* flag, cudaStream_t s) {
@@ -422,11 +470,11 @@ cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int
 }
 
 cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
-                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s) {
+                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth) {
   size_t sm = (size_t)max_n * (sizeof(c64) + sizeof(int));
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_gj_colperm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gj_colperm<<<dim3(nmat, ne), 256, sm, s>>>(probs, F, f_es, piv, piv_es);
+  k_gj_colperm<<<dim3(nmat, ne), 256, sm, s>>>(probs, F, f_es, piv, piv_es, growth);
   return cudaGetLastError();
 }
 

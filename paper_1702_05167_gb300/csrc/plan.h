@@ -78,6 +78,7 @@ struct Input {
   const int64_t* contact_ptr = nullptr;
   const int32_t* contact_sites = nullptr;
   int dims[3] = {0, 0, 0};   // all zero: general graph bisection
+  int variant = 0;           // 1..4: alternate separator trees (cuts below the root moved +1, -1, +2, -2)
 };
 
 // Builds the plan. Returns an empty string on success, else an error message.

@@ -12,6 +12,7 @@
 //   downward  G_iU = -X G_UU;  G_ii = D^{-1} - X G_iU^T                        (Algorithm 1)
 //             W = D^{-1} [L_ii conj(G_ii) + L_iU conj(G_Ui) | L_ii conj(G_iU) + L_iU conj(G_UU)]
 //             P_iU = W_iU - X P_UU;  P_ii = W_ii + X P_iU^dagger              (Algorithm 2)
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -54,11 +55,11 @@ struct DownLevel {
 };
 
 enum KClass { K_GEMM = 0, K_GEMM_TC, K_SCHUR, K_SCHUR_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
-              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_NCLASS };
+              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_RESID, K_NCLASS };
 static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "schur_z_dmma",
                                            "schur_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
                                            "assemble", "add_a", "lesser_fold", "gather", "out",
-                                           "gemm_z_ozaki", "schur_z_ozaki"};
+                                           "gemm_z_ozaki", "schur_z_ozaki", "residual"};
 
 struct Prof {
   bool on = false;
@@ -90,6 +91,8 @@ struct DeviceState {
   GemmProb* gpoz = nullptr;
   int32_t *maps = nullptr, *h_rq = nullptr, *own_contact = nullptr;
   int64_t *h_vi = nullptr, *doff = nullptr;
+  int64_t *res_rowptr = nullptr, *res_loc = nullptr;   // residual check: CSR rows, G location per entry
+  int32_t* unk_slot = nullptr;                          // contact slot of each unknown, or -1
   c64* hval = nullptr;
   int32_t *u_owner = nullptr, *u_local = nullptr, *u_seg = nullptr, *posmap = nullptr;
   int* flag = nullptr;
@@ -103,7 +106,10 @@ struct DeviceState {
   bool use_pack = true;              // HSC_MIXED: pack operands once per launch (else per tile)
   // workspace for `cap` energies
   int64_t cap = 0;
-  void* arena = nullptr;
+  void* arena = nullptr;             // owned workspace (nullptr while borrowing)
+  size_t arena_bytes = 0;
+  void* borrow = nullptr;            // alternate-tree handles: the main handle's idle workspace
+  size_t borrow_bytes = 0;
   c64 *F = nullptr, *L = nullptr, *G = nullptr, *P = nullptr, *S = nullptr, *LS = nullptr,
       *X = nullptr, *T = nullptr, *Z = nullptr, *GUU = nullptr, *PUU = nullptr, *N = nullptr,
       *GJT = nullptr;
@@ -118,6 +124,15 @@ struct DeviceState {
   int64_t* slot_unknown = nullptr;   // contact slot -> unknown (observables)
   int32_t* slot_contact = nullptr;   // contact slot -> contact id
   cudaStream_t branch = nullptr;
+  // per energy of the last solve: growth (largest |Re| + |Im| of any D_i^{-1} entry) and residual
+  // (largest |(A G^r - I)_uu|); one allocation, resid = growth + growth_cap
+  float* growth = nullptr;
+  float* resid = nullptr;
+  int64_t growth_cap = 0, growth_n = 0;
+  float* growth_wave = nullptr;      // the current wave's slices
+  float* resid_wave = nullptr;
+  void* rs_buf = nullptr;            // device staging of re-solved energies (device-io solves)
+  size_t rs_cap = 0;
   std::vector<void*> fixed;          // energy-independent allocations
 };
 
@@ -134,6 +149,8 @@ void device_state_free(DeviceState* d) {
   if (d->slot_unknown) cudaFree(d->slot_unknown);
   if (d->slot_contact) cudaFree(d->slot_contact);
   if (d->branch) cudaStreamDestroy(d->branch);
+  if (d->growth) cudaFree(d->growth);
+  if (d->rs_buf) cudaFree(d->rs_buf);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
 }
@@ -247,6 +264,8 @@ struct GemmList {
 // 16-byte boundary
 int64_t oz_scale_word(const GemmArgs& g) { return ((g.pack_words + 1) / 2 + 3) / 4 * 4; }
 int64_t oz_words(const GemmArgs& g) { return oz_scale_word(g) + 2 * g.scale_vals; }
+
+int locate_pair(const Plan& P, int64_t a, int64_t b, int64_t* out);
 
 int build_schedule(hsc_ctx* h) {
   DeviceState* d = h->dev;
@@ -523,6 +542,18 @@ int build_schedule(hsc_ctx* h) {
   }
   std::vector<c64> hv(h->val.size());
   for (size_t k = 0; k < hv.size(); ++k) hv[k] = make_double2(h->val[k].re, h->val[k].im);
+  // residual check: location of G_uv for every non-zero (u, v), contact slot of every unknown
+  std::vector<int64_t> rloc(h->col.size());
+  for (int64_t u = 0; u < P.n; ++u)
+    for (int64_t k = h->rowptr[u]; k < h->rowptr[u + 1]; ++k) {
+      int64_t off = 0;
+      if (!locate_pair(P, u, h->col[k], &off))
+        return hsc_fail(h, HSC_ERR_ARG, "an H entry lies outside the selected pattern");
+      rloc[k] = off >= 0 ? off : -off - 1;   // G^r is complex symmetric
+    }
+  std::vector<int32_t> uslot(P.n, -1);
+  for (int64_t u = 0; u < P.n; ++u)
+    uslot[u] = P.own_contact[P.own_off[P.unk_cluster[u]] + P.unk_local[u]];
 
   cudaError_t e = cudaSuccess;
 #define UP(dst, v) if ((e = upload(d, dst, v)) != cudaSuccess) return hsc_fail(h, HSC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e))
@@ -542,6 +573,9 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->u_seg, P.u_seg);
   UP(&d->posmap, P.posmap);
   UP(&d->doff, doff);
+  UP(&d->res_rowptr, h->rowptr);
+  UP(&d->res_loc, rloc);
+  UP(&d->unk_slot, uslot);
 #undef UP
   if ((e = cudaMalloc((void**)&d->flag, 4 * sizeof(int))) != cudaSuccess)
     return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc flag");
@@ -579,14 +613,25 @@ int ensure_arena(hsc_ctx* h, int64_t want, int64_t pack_words) {
   if (d->cap >= want && d->pk_cur >= pack_words) return HSC_OK;
   want = std::max(want, d->cap);
   pack_words = std::max(pack_words, d->pk_cur);
-  if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->cap = 0; d->pk_cur = 0; d->PK = nullptr; }
+  if (d->arena) { cudaFree(d->arena); d->arena = nullptr; d->arena_bytes = 0; }
+  d->cap = 0;
+  d->pk_cur = 0;
+  d->PK = nullptr;
   size_t bytes = (size_t)bytes_per_energy(d, pack_words) * want + 64 * 256;
-  cudaError_t e = cudaMalloc(&d->arena, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc workspace (" + std::to_string(bytes >> 20) + " MiB)");
+  char* p;
+  if (d->borrow) {
+    if (bytes > d->borrow_bytes)
+      return hsc_fail(h, HSC_ERR_OOM, "borrowed workspace too small (" + std::to_string(bytes >> 20) + " MiB)");
+    p = (char*)d->borrow;
+  } else {
+    cudaError_t e = cudaMalloc(&d->arena, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc workspace (" + std::to_string(bytes >> 20) + " MiB)");
+    }
+    d->arena_bytes = bytes;
+    p = (char*)d->arena;
   }
-  char* p = (char*)d->arena;
   auto take = [&](int64_t elems, size_t esz) {
     char* r = p;
     p += ((size_t)elems * want * esz + 255) / 256 * 256;
@@ -707,7 +752,8 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       tc = keep;
     }
     LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
-           launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s));
+           launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s,
+                             d->growth_wave));
     GEMM(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0);
     schur = true;
     GEMM(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es);
@@ -743,6 +789,10 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
     GEMM(D.d[8], d->X, d->x_es, d->P, d->aug_es, d->P, d->aug_es, d->P, d->aug_es);
   }
 #undef GEMM
+  if (d->resid_wave)
+    LAUNCH(K_RESID, 1, 0.0, 0.0,
+           launch_residual(h->n, d->res_rowptr, d->hval, d->res_loc, d->doff, d->unk_slot, E, eta, sr,
+                           ncs, d->G, d->aug_es, d->resid_wave, ne, s));
   LAUNCH(K_OUT, npair > 0 ? 2 : 1, 0.0, 32.0 * (double)(h->n + npair) * ne * (les ? 2 : 1),
          launch_out(d->doff, h->n, poff, npair, d->G, d->P, d->aug_es, ogr, les ? ogl : nullptr, pgr,
                     les ? pgl : nullptr, ne, s));
@@ -893,6 +943,7 @@ int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out, 
   DeviceState* d = h->dev;
   const int64_t pack = pack_words_needed(d, precision);
   const int64_t per = bytes_per_energy(d, pack);
+  if (d->borrow) byte_cap = std::min<int64_t>(byte_cap, (int64_t)d->borrow_bytes - 64 * 256);
   int64_t wave = std::min<int64_t>(n_E, std::max<int64_t>(byte_cap / per, 0));
   if (d->cap > 0) wave = std::max<int64_t>(std::min<int64_t>(n_E, d->cap), wave);
   if (wave <= 0) return hsc_fail(h, HSC_ERR_OOM, "one energy needs " + std::to_string(per >> 20) + " MiB of workspace");
@@ -900,6 +951,22 @@ int prepare_arena(hsc_ctx* h, int64_t n_E, int64_t byte_cap, int64_t* wave_out, 
   int rc = ensure_arena(h, wave, pack);
   if (rc != HSC_OK) return rc;
   *wave_out = wave;
+  return HSC_OK;
+}
+
+// Sizes the per-energy growth record for a solve of n_E energies (before any capture).
+int ensure_growth(hsc_ctx* h, int64_t n_E) {
+  DeviceState* d = h->dev;
+  if (d->growth_cap < n_E) {
+    if (d->growth) cudaFree(d->growth);
+    d->growth = nullptr;
+    d->growth_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&d->growth, 2 * std::max<int64_t>(n_E, 1) * sizeof(float));
+    if (e != cudaSuccess) { cudaGetLastError(); return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc growth"); }
+    d->growth_cap = std::max<int64_t>(n_E, 1);
+  }
+  d->resid = d->growth + d->growth_cap;
+  d->growth_n = n_E;
   return HSC_OK;
 }
 
@@ -911,8 +978,12 @@ int enqueue_device(hsc_ctx* h, int64_t n_E, int64_t wave, const double* E, doubl
   DeviceState* d = h->dev;
   const int64_t n = h->n, ncs = h->n_contact_unknowns;
   CK(cudaMemsetAsync(d->flag, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(d->growth, 0, n_E * sizeof(float), s));
+  CK(cudaMemsetAsync(d->resid, 0, n_E * sizeof(float), s));
   for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
     const int ne = (int)std::min<int64_t>(wave, n_E - e0);
+    d->growth_wave = d->growth + e0;
+    d->resid_wave = d->resid + e0;
     const c64* dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
     const c64* dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
     c64* ogr = reinterpret_cast<c64*>(diag_gr) + e0 * n;
@@ -938,6 +1009,112 @@ int read_flags(hsc_ctx* h, cudaStream_t s) {
 }  // namespace
 }  // namespace hsc
 
+namespace hsc {
+namespace {
+
+// Energies whose residual |(A G^r - I)_uu| exceeds the handle's threshold are solved again on the
+// alternate separator tree v; per energy, the result of the tree with the smaller residual is kept
+// (outputs and both records overwritten in place). Inputs and outputs are where the caller's
+// hsc_solve had them.
+int resolve_grown(int v, hsc_ctx* h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                  const hsc_c128* sigma_less, int32_t precision, int32_t n_req, const int32_t* req_pairs,
+                  hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl,
+                  cudaStream_t s, bool dev_io) {
+  DeviceState* d = h->dev;
+  std::vector<float> r(n_E);
+  CK(cudaMemcpyAsync(r.data(), d->resid, n_E * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const float thr = (float)std::pow(10.0, -h->opt_resolve);
+  std::vector<int64_t> J;
+  for (int64_t k = 0; k < n_E; ++k)
+    if (!(r[k] <= thr)) J.push_back(k);
+  if (J.empty()) return HSC_OK;
+  hsc_ctx* a = hsc_alt(h, v);
+  if (!a || get_state(a) != HSC_OK) return HSC_OK;   // no alternate tree: the results so far stand
+  {
+    // the main solve is complete on this stream, so its workspace holds nothing live: the alternate
+    // tree works in it (several alternates could not each own a workspace of that size)
+    DeviceState* ad = a->dev;
+    if (ad->arena) { cudaFree(ad->arena); ad->arena = nullptr; ad->arena_bytes = 0; }
+    ad->borrow = d->arena;
+    ad->borrow_bytes = d->arena_bytes;
+    ad->cap = 0;
+    ad->pk_cur = 0;
+    ad->PK = nullptr;
+  }
+  const int64_t nj = (int64_t)J.size(), n = h->n, ncs = h->n_contact_unknowns;
+  const bool les = sigma_less != nullptr;
+  const int64_t nq = n_req;
+  // staging: E, Sigma^r, Sigma^< in; diag G^r, diag G^<, pairs out (host or device, as the caller's)
+  const size_t bytes = nj * (8 + 16 * (ncs * (les ? 2 : 1) + (n + nq) * (les ? 2 : 1))) + 8 * 256;
+  std::vector<char> hbuf;
+  char* base;
+  if (dev_io) {
+    if (d->rs_cap < bytes) {
+      if (d->rs_buf) cudaFree(d->rs_buf);
+      d->rs_buf = nullptr;
+      d->rs_cap = 0;
+      cudaError_t e = cudaMalloc(&d->rs_buf, bytes);
+      if (e != cudaSuccess) { cudaGetLastError(); return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc re-solve staging"); }
+      d->rs_cap = bytes;
+    }
+    base = (char*)d->rs_buf;
+  } else {
+    hbuf.resize(bytes);
+    base = hbuf.data();
+  }
+  char* p = base;
+  auto take = [&](int64_t b) { char* r = p; p += (b + 255) / 256 * 256; return r; };
+  double* sE = (double*)take(nj * 8);
+  hsc_c128* ssr = (hsc_c128*)take(nj * ncs * 16);
+  hsc_c128* ssl = les ? (hsc_c128*)take(nj * ncs * 16) : nullptr;
+  hsc_c128* sgr = (hsc_c128*)take(nj * n * 16);
+  hsc_c128* sgl = les ? (hsc_c128*)take(nj * n * 16) : nullptr;
+  hsc_c128* spr = nq ? (hsc_c128*)take(nj * nq * 16) : nullptr;
+  hsc_c128* spl = (nq && les) ? (hsc_c128*)take(nj * nq * 16) : nullptr;
+  const cudaMemcpyKind kind = dev_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToHost;
+  int rc = HSC_OK;
+  auto copy = [&](void* dst, const void* src, size_t b) -> bool {
+    if (b == 0) return true;
+    if (!dev_io) { std::memcpy(dst, src, b); return true; }
+    return cudaMemcpyAsync(dst, src, b, kind, s) == cudaSuccess;
+  };
+  for (int64_t j = 0; j < nj && rc == HSC_OK; ++j) {
+    const int64_t k = J[j];
+    bool ok = copy(sE + j, E + k, 8) && copy(ssr + j * ncs, sigma_r + k * ncs, ncs * 16);
+    if (les) ok = ok && copy(ssl + j * ncs, sigma_less + k * ncs, ncs * 16);
+    if (!ok) rc = hsc_fail(h, HSC_ERR_CUDA, "re-solve gather");
+  }
+  const int src = rc == HSC_OK ? hsc_solve(a, nj, sE, eta, ncs ? ssr : nullptr, ssl, precision, n_req, req_pairs,
+                                           sgr, sgl, spr, spl, s, dev_io ? 1 : 0) : -1;
+  if (rc == HSC_OK && src == HSC_OK) {
+    std::vector<double> ra(nj), ga(nj);
+    if (hsc_residual(a, nj, ra.data()) == HSC_OK && hsc_growth(a, nj, ga.data()) == HSC_OK) {
+      for (int64_t j = 0; j < nj && rc == HSC_OK; ++j) {
+        const int64_t k = J[j];
+        if (!((float)ra[j] < r[k])) continue;
+        bool ok = copy(diag_gr + k * n, sgr + j * n, n * 16);
+        if (les) ok = ok && copy(diag_gl + k * n, sgl + j * n, n * 16);
+        if (nq) ok = ok && copy(req_gr + k * nq, spr + j * nq, nq * 16);
+        if (nq && les) ok = ok && copy(req_gl + k * nq, spl + j * nq, nq * 16);
+        r[k] = (float)ra[j];
+        const float gk = (float)ga[j];
+        ok = ok && cudaMemcpyAsync(d->resid + k, &r[k], sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+             cudaMemcpy(d->growth + k, &gk, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (!ok) rc = hsc_fail(h, HSC_ERR_CUDA, "re-solve scatter");
+      }
+    }
+  }
+  // an alternate solve that failed (e.g. a requested pair outside its pattern) leaves the first
+  // results in place
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (rc == HSC_OK && e != cudaSuccess) rc = hsc_fail(h, HSC_ERR_CUDA, cudaGetErrorString(e));
+  return rc;
+}
+
+}  // namespace
+}  // namespace hsc
+
 extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
                          const hsc_c128* sigma_less, int32_t precision, int32_t n_req,
                          const int32_t* req_pairs, hsc_c128* diag_gr, hsc_c128* diag_gl,
@@ -951,6 +1128,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
   DeviceState* d = h->dev;
   int64_t wave = 0;
   if ((rc = prepare_arena(h, n_E, budget_bytes(), &wave, precision)) != HSC_OK) return rc;
+  if ((rc = ensure_growth(h, n_E)) != HSC_OK) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (io_on_device) {
     rc = enqueue_device(h, n_E, wave, E, eta, sigma_r, sigma_less, precision, n_req, diag_gr, diag_gl,
@@ -977,8 +1155,12 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     c64* spr = (c64*)take(wave * (int64_t)n_req * 16);
     c64* spl = (c64*)take(wave * (int64_t)n_req * 16);
     CK(cudaMemsetAsync(d->flag, 0, 4 * sizeof(int), s));
+    CK(cudaMemsetAsync(d->growth, 0, n_E * sizeof(float), s));
+    CK(cudaMemsetAsync(d->resid, 0, n_E * sizeof(float), s));
     for (int64_t e0 = 0; e0 < n_E; e0 += wave) {
       const int ne = (int)std::min<int64_t>(wave, n_E - e0);
+      d->growth_wave = d->growth + e0;
+      d->resid_wave = d->resid + e0;
       CK(cudaMemcpyAsync(sE, E + e0, ne * 8, cudaMemcpyHostToDevice, s));
       if (ncs > 0) {
         CK(cudaMemcpyAsync(ssr, sigma_r + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
@@ -996,6 +1178,12 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     }
   }
   if ((rc = read_flags(h, s)) != HSC_OK) return rc;
+  if (h->opt_resolve > 0 && !h->is_alt && precision == HSC_FP64)
+    for (int v = 1; v <= 4; ++v)
+      if (v != h->nd_variant &&
+          (rc = hsc::resolve_grown(v, h, n_E, E, eta, sigma_r, sigma_less, precision, n_req, req_pairs,
+                                   diag_gr, diag_gl, req_gr, req_gl, s, io_on_device != 0)) != HSC_OK)
+        return rc;
   h->err.clear();
   return HSC_OK;
 }
@@ -1144,6 +1332,25 @@ extern "C" int hsc_debug_gemm(int32_t engine, int32_t opa, int32_t opb, int32_t 
   return HSC_OK;
 }
 
+namespace hsc {
+namespace {
+int read_record(hsc_ctx* h, int64_t n_E, double* out, bool residual) {
+  if (!h || (!out && n_E > 0) || n_E < 0) return hsc_fail(h, HSC_ERR_ARG, "bad arguments");
+  DeviceState* d = h->dev;
+  if (!d || !d->growth || n_E > d->growth_n)
+    return hsc_fail(h, HSC_ERR_STATE, "no solve of that many energies has run on this handle");
+  std::vector<float> g(n_E);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(g.data(), residual ? d->resid : d->growth, n_E * sizeof(float), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < n_E; ++k) out[k] = g[k];
+  return HSC_OK;
+}
+}  // namespace
+}  // namespace hsc
+
+extern "C" int hsc_growth(hsc_t h, int64_t n_E, double* out) { return hsc::read_record(h, n_E, out, false); }
+extern "C" int hsc_residual(hsc_t h, int64_t n_E, double* out) { return hsc::read_record(h, n_E, out, true); }
+
 // ---- batched solve in one CUDA graph -----------------------------------------------------------
 
 namespace hsc {
@@ -1192,6 +1399,7 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
     hsc_ctx* h = items[i].h;
     int64_t cap = (int64_t)(budget * need[i] / need_total);
     int rc = prepare_arena(h, std::max<int64_t>(items[i].n_E, 1), cap, &wave[i], precision);
+    if (rc == HSC_OK) rc = ensure_growth(h, std::max<int64_t>(items[i].n_E, 1));
     if (rc != HSC_OK) return item_fail(i, h, rc);
     if (!h->dev->branch) {
       cudaError_t e = cudaStreamCreateWithFlags(&h->dev->branch, cudaStreamNonBlocking);
@@ -1209,7 +1417,7 @@ extern "C" int hsc_solve_batch(int32_t n_items, const hsc_batch_item* items, dou
   for (int i = 0; i < n_items; ++i) {
     const hsc_batch_item& it = items[i];
     DeviceState* d = it.h->dev;
-    for (uint64_t v : {u64(it.h), d->gen, u64(d->arena), (uint64_t)d->cap, (uint64_t)it.n_E, u64(it.E),
+    for (uint64_t v : {u64(it.h), d->gen, u64(d->arena), (uint64_t)d->cap, u64(d->growth), (uint64_t)it.n_E, u64(it.E),
                        u64(it.sigma_r), u64(it.sigma_less), (uint64_t)it.n_req, u64(d->poff),
                        u64(it.diag_gr), u64(it.diag_gl), u64(it.req_gr), u64(it.req_gl),
                        (uint64_t)wave[i]})

@@ -18,12 +18,13 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
           8: "HSC_ERR_TIMEOUT"}
 
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
-           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read",
+           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read", "hsc_growth",
+           "hsc_residual",
            "hsc_device_fp64_peaks", "hsc_observables", "hsc_last_error", "hsc_destroy",
            "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
            "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF, HSC_OPT_COMPLEX_4M = 1, 2, 3, 4, 5
-HSC_OPT_FP64_ENGINE = 6
+HSC_OPT_FP64_ENGINE, HSC_OPT_RESOLVE_DIGITS, HSC_OPT_TREE_VARIANT = 6, 7, 8
 
 
 class hsc_tree_stats(ctypes.Structure):
@@ -102,6 +103,8 @@ def load():
     L.hsc_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
     L.hsc_mlp_destroy.argtypes = [vp]
     L.hsc_profile.argtypes = [vp, i32]
+    L.hsc_growth.argtypes = [vp, i64, vp]
+    L.hsc_residual.argtypes = [vp, i64, vp]
     L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(hsc_kernel_stat), i32, ctypes.POINTER(i32)]
     L.hsc_device_fp64_peaks.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
     L.hsc_last_error.argtypes = [vp]
@@ -229,6 +232,20 @@ def hsc_tune(h, E, eta, sigma_r, sigma_less, precision=HSC_FP64, cache_path=None
                               int(precision), cp, ctypes.byref(r)))
     return dict(leaf_max=r.leaf_max, gj_panel=r.gj_panel, ms_per_energy=r.ms_per_energy,
                 from_cache=bool(r.from_cache), n_tried=r.n_tried)
+
+
+def hsc_growth(h, n_E):
+    """Per-energy element growth of the last solve: max over the cluster blocks of max |D_i^{-1}|."""
+    out = np.zeros(n_E)
+    _check(h, load().hsc_growth(h, int(n_E), _ptr(out)))
+    return out
+
+
+def hsc_residual(h, n_E):
+    """Per-energy residual of the last solve: max_u |(A G^r - I)_uu| from the computed blocks."""
+    out = np.zeros(n_E)
+    _check(h, load().hsc_residual(h, int(n_E), _ptr(out)))
+    return out
 
 
 def hsc_profile(h, enable):

@@ -74,8 +74,10 @@ def test_rejects_bad_arguments_and_state():
     hsc.hsc_destroy(h)
 
 
-def _tree(dev, leaf, geometric=True):
+def _tree(dev, leaf, geometric=True, variant=0):
     h = _handle(dev, geometric)
+    if variant:
+        hsc.hsc_set_option(h, hsc.HSC_OPT_TREE_VARIANT, variant)
     st = hsc.hsc_analyze(h, leaf)
     cl = [hsc.hsc_cluster(h, i) for i in range(st.n_clusters)]
     hsc.hsc_destroy(h)
@@ -85,11 +87,13 @@ def _tree(dev, leaf, geometric=True):
 @pytest.mark.parametrize("dims,orb,leaf,geo", [((8, 8, 8), 1, 4, True), ((9, 5, 7), 1, 3, True),
                                                ((6, 3, 2), 3, 2, True), ((7, 6, 5), 1, 2, False),
                                                ((17, 1, 1), 1, 1, True)])
-def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo):
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo, variant):
     """Every unknown is owned once; no H entry joins two unrelated clusters (separation); each U_i
-    is exactly the set of ancestor unknowns adjacent to the subtree of i (Section 2.2)."""
+    is exactly the set of ancestor unknowns adjacent to the subtree of i (Section 2.2). Holds for
+    the plain tree and both alternate trees (cuts below the root shifted)."""
     dev = W.cubic_device(dims, seed=1) if orb == 1 else W.wire_device(dims, orb=orb, seed=1)
-    st, cl = _tree(dev, leaf, geo)
+    st, cl = _tree(dev, leaf, geo, variant)
     nc = st.n_clusters
     owner = np.full(dev.n, -1)
     for i, (info, own, upd) in enumerate(cl):
@@ -128,6 +132,20 @@ def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo):
                                   any(cl[c][0].lesser for c in info.child if c >= 0))
 
 
+@pytest.mark.parametrize("dims,leaf,geo", [((32, 32, 32), 8, True), ((12, 9, 7), 3, True),
+                                           ((9, 8, 7), 2, False)])
+def test_alternate_trees_share_the_root_and_move_the_leaves(dims, leaf, geo):
+    """The alternate separator trees keep the root separator (so the coupling entries across it
+    stay in the selected pattern) and change the leaf clusters (different isolated blocks)."""
+    dev = W.cubic_device(dims, seed=2)
+    trees = [_tree(dev, leaf, geo, v)[1] for v in (0, 1, 2, 3, 4)]
+    roots = [set(t[-1][1].tolist()) for t in trees]
+    assert all(r == roots[0] for r in roots)
+    leaves = [{frozenset(own.tolist()) for info, own, _ in t if info.child[0] < 0 and info.child[1] < 0}
+              for t in trees]
+    assert all(leaves[a] != leaves[b] for a in range(5) for b in range(a))
+
+
 def test_operation_count_follows_table_1_cube_slope():
     """Table 1: the HSC-extension costs O(N^6) on an N^3 cube; the model's log-log slope between
     N = 24 and N = 48 (leaves <= 8) must be close to 6 (and far from RGF's 7)."""
@@ -155,7 +173,14 @@ def test_options_round_trip_and_reject_bad_values():
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF) == 2
     hsc.hsc_set_option(h, hsc.HSC_OPT_GJ_PANEL, 8)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 8
-    for opt, val in ((hsc.HSC_OPT_GJ_PANEL, 0), (hsc.HSC_OPT_GJ_PANEL, 65), (99, 1)):
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_RESOLVE_DIGITS) == 4
+    hsc.hsc_set_option(h, hsc.HSC_OPT_FP64_ENGINE, 2)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_FP64_ENGINE) == 2
+    hsc.hsc_set_option(h, hsc.HSC_OPT_RESOLVE_DIGITS, 8)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_RESOLVE_DIGITS) == 8
+    for opt, val in ((hsc.HSC_OPT_GJ_PANEL, 0), (hsc.HSC_OPT_GJ_PANEL, 65), (99, 1),
+                     (hsc.HSC_OPT_FP64_ENGINE, 3), (hsc.HSC_OPT_RESOLVE_DIGITS, 16),
+                     (hsc.HSC_OPT_TREE_VARIANT, 5)):
         with pytest.raises(hsc.HSCError) as ei:
             hsc.hsc_set_option(h, opt, val)
         assert ei.value.code == hsc.HSC_ERR_ARG
