@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-schur48", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the batch8 workload")
     p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E", "batch8"],
@@ -120,17 +121,18 @@ def workload(rank, ws, name="cubic32"):
     return cfg
 
 
-def cpu_oracle_energy(cfg, k):
-    """One energy of the workload by the RGF oracle; returns seconds."""
+def cpu_oracle_energy(cfg, k, want_output=False):
+    """One energy of the workload by the RGF oracle; returns seconds (and the oracle's output)."""
     from oracle import rgf
     from paper_1702_05167_gb300 import workloads as W
     dev = cfg["dev"]
     sr, sl = W.self_energies(dev, 1, cfg["f"])
     H = dev.to_scipy()
     t0 = time.perf_counter()
-    rgf.sweep(H, dev.dims[1] * dev.dims[2] * dev.orb, cfg["energies"][k], cfg["eta"],
-              dev.contact_unknowns(), sr[0], sl[0], coupling_layers=(15,))
-    return time.perf_counter() - t0
+    out = rgf.sweep(H, dev.dims[1] * dev.dims[2] * dev.orb, cfg["energies"][k], cfg["eta"],
+                    dev.contact_unknowns(), sr[0], sl[0], coupling_layers=(15,))
+    t = time.perf_counter() - t0
+    return (t, out) if want_output else t
 
 
 def run_reference(args):
@@ -218,6 +220,8 @@ def run_hsc(args):
     ms = t0.elapsed_time(t1)
     prof = hsc.hsc_profile_read(h)
     hsc.hsc_profile(h, False)
+    growth = hsc.hsc_growth(h, nE)
+    resid = hsc.hsc_residual(h, nE)
     if ws > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dvc)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -252,26 +256,46 @@ def run_hsc(args):
                "h2d_bytes_per_step": int(hE.nbytes + hsr.nbytes + hsl.nbytes + 8 * npair),
                "d2h_bytes_per_step": int(hgr.nbytes + hgl.nbytes + hpr.nbytes + hpl.nbytes)}
 
-    # ---- roofline of the dominant kernel class (complex GEMM on the FP64 tensor pipe) ----
+    # ---- roofline of the dominant kernel class ----
     dmma, dfma = hsc.hsc_device_fp64_peaks()
-    g = {k: sum(p[k] for p in prof if p["name"] in ("gemm_z_dmma", "schur_z_dmma"))
-         for k in ("flops", "ms", "timed", "launches")}
     tot_ms = sum(p["ms"] for p in prof)
-    achieved = g["flops"] / (g["ms"] / 1000.0) / 1e12 if g["ms"] > 0 else 0.0
-    peak = dmma / 1000.0
-    roof = {"kernel": "k_gemm_z (grouped complex128 GEMM, mma.sync m8n8k4 f64, 3 real products "
-                      "per complex product)", "bound": "tensor",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    cls = lambda names: {k: sum(p[k] for p in prof if p["name"] in names)
+                         for k in ("flops", "ms", "timed", "launches")}
+    gz = cls(("gemm_z_dmma", "schur_z_dmma"))
+    go = cls(("gemm_z_ozaki", "schur_z_ozaki"))
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)
+    rate = lambda g: g["flops"] / (g["ms"] / 1000.0) / 1e12 if g["ms"] > 0 else 0.0
+    fp64_pipe = {"kernel": "k_gemm_z (grouped complex128 GEMM, mma.sync m8n8k4 f64, 3 real products "
+                           "per complex product)", "bound": "tensor",
+                 "achieved": rate(gz), "peak": dmma / 1000.0, "unit": "TFLOP/s",
+                 "frac": rate(gz) / (dmma / 1000.0), "traffic": None,
+                 "flop_convention": "8 real flops per complex multiply-add (algorithmic); the 3M kernel "
+                                    "executes 6 of them, so frac can exceed 1",
+                 "pipe_frac": rate(gz) * 0.75 / (dmma / 1000.0),
+                 "peak_source": "FP64 tensor-pipe throughput probe (hsc_device_fp64_peaks) on this GPU in "
+                                "this run; MEASURED_PEAKS.json has no FP64 figure",
+                 "scalar_fp64_peak_tflops": dfma / 1000.0,
+                 "share_of_device_time": gz["ms"] / tot_ms if tot_ms > 0 else None,
+                 "launches": gz["timed"], "avg_launch_ms": gz["ms"] / max(gz["timed"], 1)}
+    # FP64 emulation: 36 slice products x 3 real products x 2 flops per complex MAC = 27 x the
+    # 8-flop complex count, executed as BF16 MMAs
+    oz_bf16 = 27.0 * rate(go)
+    emul = {"kernel": "k_gemm_oz (+k_oz_pack): complex128 GEMM emulated on the BF16 tensor cores "
+                      "(tcgen05.mma kind::f16, 8 exact 7-bit slices per operand, FP32 TMEM "
+                      "accumulators drained to FP64 every 128 K values)", "bound": "tensor",
+            "achieved": oz_bf16, "peak": bf16_sust, "unit": "TFLOP/s", "frac": oz_bf16 / bf16_sust,
             "traffic": None,
-            "flop_convention": "achieved counts 8 real flops per complex multiply-add (the algorithmic "
-                               "complex GEMM count); the 3M kernel executes 6 of them on the FP64 pipe, "
-                               "so frac can exceed 1",
-            "pipe_frac": achieved * 0.75 / peak,
-            "peak_source": "FP64 tensor-pipe throughput probe (hsc_device_fp64_peaks) on this GPU "
-                           "in this run; MEASURED_PEAKS.json has no FP64 figure",
-            "scalar_fp64_peak_tflops": dfma / 1000.0,
-            "share_of_device_time": g["ms"] / tot_ms if tot_ms > 0 else None,
-            "launches": g["timed"], "avg_launch_ms": g["ms"] / max(g["timed"], 1)}
+            "flop_convention": "BF16 MMA flops the scheme needs: 36 slice pairs x 3 real products x "
+                               "2 M N K per complex GEMM (27 x the 8-flop complex count), no padding",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+            "fp64_equivalent_tflops": rate(go),
+            "fp64_equivalent_vs_fp64_pipe_peak": rate(go) / (dmma / 1000.0),
+            "share_of_device_time": go["ms"] / tot_ms if tot_ms > 0 else None,
+            "launches": go["timed"], "avg_launch_ms": go["ms"] / max(go["timed"], 1)}
+    roof, other = (emul, fp64_pipe) if go["ms"] >= gz["ms"] else (fp64_pipe, emul)
+    roof = dict(roof, secondary_gemm_class=other)
     kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
                            "share": round(p["ms"] / tot_ms, 4) if tot_ms else None}
                for p in prof}
@@ -312,6 +336,9 @@ def run_hsc(args):
                              if tcp["ms"] > 0 else None, "ms": tcp["ms"], "launches": tcp["launches"]},
                  "note": "3xTF32 tcgen05 products below the top 2 tree levels; eta = 1e-6 makes "
                          "the elimination growth ~1e7, so this mode is not accurate on this workload"}
+
+    # the secondary measurements below each need a workspace of their own: release the main one
+    solver.close()
 
     # ---- the autotuner's choice on the same workload (identical outputs; leaf size and panel
     #      width chosen by timing probe energies) ----
@@ -368,14 +395,50 @@ def run_hsc(args):
                    "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio (1.1/2.25)",
                    "launches": sc["launches"], "ms": sc["ms"]}
 
+    # ---- secondary: the plain separator tree only (no residual-driven re-solve) ----
+    plain = None
+    if rank == 0 and not args.no_plain:
+        sp = hsc.Solver(dev, cfg["leaf"])
+        hsc.hsc_set_option(sp.h, hsc.HSC_OPT_RESOLVE_DIGITS, 0)
+        def step_p():
+            hsc.hsc_solve(sp.h, tE, cfg["eta"], tsr, tsl, hsc.HSC_FP64, pairs, ogr2, ogl2, pgr2, pgl2,
+                          stream=stream.cuda_stream, io_on_device=True)
+        ogr2, ogl2 = torch.empty_like(ogr), torch.empty_like(ogl)
+        pgr2, pgl2 = torch.empty_like(pgr), torch.empty_like(pgl)
+        step_p()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        step_p()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        pres = hsc.hsc_residual(sp.h, nE)
+        sp.close()
+        plain = {"value": nE / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "residual_max": float(pres.max()), "energies_residual_gt_1e-4": int((pres > 1e-4).sum()),
+                 "note": "same workload on the plain separator tree alone (HSC_OPT_RESOLVE_DIGITS = 0)"}
+
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
+    accuracy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t = cpu_oracle_energy(cfg, 20)
+        kq = 20
+        t, oref = cpu_oracle_energy(cfg, kq, want_output=True)
         cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "1 energy (E index 20) of the 64-energy grid, RGF sweep, complex128"}
+        # the same energy from the timed GPU solve against the oracle's output
+        Ls = dev.dims[1] * dev.dims[2]
+        u, v = pairs[:, 0] - 15 * Ls, pairs[:, 1] - 16 * Ls
+        got = [t_.cpu().numpy().view(np.complex128)[kq] for t_ in (ogr, ogl, pgr, pgl)]
+        refs = [oref["diag_gr"], oref["diag_gl"], oref["coupling_gr"][15][u, v], oref["coupling_gl"][15][u, v]]
+        errs = [float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got, refs)]
+        accuracy = {"oracle": "RGF sweep (CPU, complex128)", "energy_index": kq,
+                    "E": float(E[kq]), "eta": cfg["eta"],
+                    "max_rel_err": dict(zip(("diag_gr", "diag_gl", "gr_x15_x16", "gl_x15_x16"), errs)),
+                    "growth": float(growth[kq])}
 
-    solver.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -383,11 +446,21 @@ def run_hsc(args):
                 "config": {"workload": cfg["name"], "grid": list(dev.dims),
                            "energies_per_gpu": nE, "eta": cfg["eta"], "leaf_max": cfg["leaf"],
                            "precision": "complex128 (HSC_FP64)", "io": "device-resident",
+                           "fp64_engine": "per product list by cost model: FP64 tensor pipe or FP64 "
+                                          "emulation on the BF16 tensor cores (HSC_OPT_FP64_ENGINE = 0)",
+                           "resolve": "energies with residual |(A G^r - I)_uu| > 1e-4 re-solved on "
+                                      "alternate separator trees (HSC_OPT_RESOLVE_DIGITS = 4, default)",
                            "clusters": st.n_clusters,
                            "l2": "working set ~%.0f GB >> L2 (no flush needed)" % (st.bytes_per_energy * nE / 1e9),
                            "parallelism": f"energy-sharded x{ws}"},
                 "model_tflops": model_tflops, "model_gflop_per_energy": (st.flops_gr + st.flops_gl) / 1e9,
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "accuracy": accuracy,
+                "residual": {"max": float(resid.max()), "median": float(np.median(resid)),
+                             "energies_gt_1e-4": int((resid > 1e-4).sum()),
+                             "meaning": "per energy max_u |(A G^r - I)_uu| from the computed blocks; "
+                                        "tracks the diag G^r error vs RGF within ~1e2"},
+                "plain_tree": plain,
                 "autotuned": tuned, "mixed_precision": mixed, "schur_updates_48cube_tensor": schur48,
                 "gpu_launches": launches, "clocks": ck}
         print(json.dumps(line))

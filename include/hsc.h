@@ -129,7 +129,7 @@ int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
  * schedule and workspace (rebuilt by the next solve). HSC_OPT_LEAF is read-only (the leaf_max of
  * the last hsc_analyze). */
 typedef enum {
-  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 16)                   */
+  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 64)                   */
   HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
   HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
   HSC_OPT_LEAF = 4,           /* read only                                                      */
@@ -200,7 +200,7 @@ typedef struct {
 } hsc_tune_result;
 
 /* hsc_tune -- autotune a handle for its geometry on this GPU: for each candidate leaf_max (4, 6, 8,
- *   when smaller than the grid) and Gauss-Jordan panel width (8, 16, 32) re-analyse, solve the given
+ *   when smaller than the grid) and Gauss-Jordan panel width (16, 32, 64) re-analyse, solve the given
  *   probe energies twice (host buffers, as hsc_solve) and time the second solve with CUDA events;
  *   keep the fastest, leave the handle analysed with it, and append one JSON line (GPU name, grid,
  *   orbitals, precision, choice, time) to cache_path (may be NULL: no cache). A matching cache line

@@ -68,6 +68,7 @@ struct Prof {
   std::vector<int> cls;
   std::vector<double> flops, bytes;
   int64_t launches[K_NCLASS] = {0};
+  hsc_kernel_stat extra[K_NCLASS] = {};   // kernels of alternate-tree re-solves, merged in
 };
 
 static uint64_t g_generation = 0;   // distinguishes device states across re-creation
@@ -77,7 +78,7 @@ struct DeviceState {
   uint64_t gen = ++g_generation;
   Prof prof;
   bool planned = false;
-  int nb = 16;                       // Gauss-Jordan panel width
+  int nb = 64;                       // Gauss-Jordan panel width
   int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
   bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
   bool four_products = false;        // FP64 engine: 4 real products per complex product (else 3M)
@@ -1035,6 +1036,7 @@ int resolve_grown(int v, hsc_ctx* h, int64_t n_E, const double* E, double eta, c
     // the main solve is complete on this stream, so its workspace holds nothing live: the alternate
     // tree works in it (several alternates could not each own a workspace of that size)
     DeviceState* ad = a->dev;
+    if (hsc_profile(a, d->prof.on ? 1 : 0) != HSC_OK) return HSC_OK;   // profile with the main handle
     if (ad->arena) { cudaFree(ad->arena); ad->arena = nullptr; ad->arena_bytes = 0; }
     ad->borrow = d->arena;
     ad->borrow_bytes = d->arena_bytes;
@@ -1088,6 +1090,19 @@ int resolve_grown(int v, hsc_ctx* h, int64_t n_E, const double* E, double eta, c
   const int src = rc == HSC_OK ? hsc_solve(a, nj, sE, eta, ncs ? ssr : nullptr, ssl, precision, n_req, req_pairs,
                                            sgr, sgl, spr, spl, s, dev_io ? 1 : 0) : -1;
   if (rc == HSC_OK && src == HSC_OK) {
+    {   // the alternate's kernels count in the main handle's profile
+      int32_t nc = 0;
+      hsc_kernel_stat st[K_NCLASS];
+      if (hsc_profile_read(a, st, K_NCLASS, &nc) == HSC_OK)
+        for (int c = 0; c < nc && c < K_NCLASS; ++c) {
+          hsc_kernel_stat& x = d->prof.extra[c];
+          x.launches += st[c].launches;
+          x.timed += st[c].timed;
+          x.ms += st[c].ms;
+          x.flops += st[c].flops;
+          x.bytes += st[c].bytes;
+        }
+    }
     std::vector<double> ra(nj), ga(nj);
     if (hsc_residual(a, nj, ra.data()) == HSC_OK && hsc_growth(a, nj, ga.data()) == HSC_OK) {
       for (int64_t j = 0; j < nj && rc == HSC_OK; ++j) {
@@ -1237,6 +1252,7 @@ extern "C" int hsc_profile(hsc_t h, int32_t enable) {
   p.flops.clear();
   p.bytes.clear();
   for (auto& l : p.launches) l = 0;
+  for (auto& x : p.extra) x = hsc_kernel_stat{};
   return HSC_OK;
 }
 
@@ -1262,7 +1278,13 @@ extern "C" int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int3
     out[p.cls[k]].flops += p.flops[k];
     out[p.cls[k]].bytes += p.bytes[k];
   }
-  for (int c = 0; c < K_NCLASS; ++c) out[c].launches = p.launches[c];
+  for (int c = 0; c < K_NCLASS; ++c) {
+    out[c].launches = p.launches[c] + p.extra[c].launches;
+    out[c].timed += p.extra[c].timed;
+    out[c].ms += p.extra[c].ms;
+    out[c].flops += p.extra[c].flops;
+    out[c].bytes += p.extra[c].bytes;
+  }
   return HSC_OK;
 }
 
@@ -1550,10 +1572,10 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
     if (l < maxdim) leaves.push_back(l);
   if (leaves.empty()) leaves.push_back(h->leaf_max > 0 ? h->leaf_max : 4);
   double best = 1e300;
-  int best_leaf = leaves[0], best_nb = 16, tried = 0;
+  int best_leaf = leaves[0], best_nb = 64, tried = 0;
   (void)ncs;
   for (int leaf : leaves)
-    for (int nb : {8, 16, 32}) {
+    for (int nb : {16, 32, 64}) {
       int rc = hsc_analyze(h, leaf, nullptr);
       if (rc == HSC_OK) rc = hsc_set_option(h, HSC_OPT_GJ_PANEL, nb);
       if (rc == HSC_OK)
