@@ -15,7 +15,10 @@
 //   * a slice product t_s u_r is an integer below 2^14 and carries the weight 2^(-7 (s + r)); the
 //     products of one diagonal d = s + r (d <= OZ_S + 1: 36 pairs) accumulate in one FP32 tensor-
 //     memory accumulator, exact for 128 K values (at most 8 pairs: 8 * 127^2 * 128 < 2^24); every
-//     128 K values the 8 accumulators are drained into FP64 registers with their weights;
+//     128 K values the 8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe
+//     would otherwise bound the kernel), into the 96-bit integer T 2^63 = H 2^32 + L per element
+//     (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)); T = H 2^-31 + L 2^-63 once
+//     per product, the only rounding;
 //   * per K value the error is below 2^-52.8 sigma_i tau_j: 2 * 2^-56 from the truncation and
 //     2^-53.1 from the dropped diagonals d >= 10 (7 * 127^2 * 2^-70 for d = 10, less beyond).
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
@@ -329,9 +332,12 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
     const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
     const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
     const int col0 = tn * OZ_BN + half * OZ_DCOLS;
-    double acc64[OZ_DCOLS];
+    // exact running sum T 2^63 = H 2^32 + L of the chunks; |H| < nchunk 2^41.1, exact in FP64 for
+    // nchunk < 2^11 (K < 262144)
+    long long H[OZ_DCOLS];
+    unsigned int L[OZ_DCOLS];
 #pragma unroll
-    for (int j = 0; j < OZ_DCOLS; ++j) acc64[j] = 0.0;
+    for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
     if (ks == 0 && row < P.M) {   // C = beta D
       for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
         c64 o = make_double2(0.0, 0.0);
@@ -352,21 +358,37 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int dg = 0; dg < OZ_ND; ++dg) {
-        const double w = __longlong_as_double((long long)(1023 - OZ_BITS * (dg + 2)) << 52);   // 2^(-7(dg+2))
+      for (int c0 = 0; c0 < OZ_DCOLS; c0 += 4) {
+        long long b[4];   // this chunk's diagonals 3..7 of 4 columns: sum v_d 2^(49 - 7 d) < 2^52.1
 #pragma unroll
-        for (int c0 = 0; c0 < OZ_DCOLS; c0 += 16) {
-          uint32_t r[16];
+        for (int j = 0; j < 4; ++j) b[j] = 0;
+#pragma unroll
+        for (int dg = 0; dg < OZ_ND; dg += 2) {   // diagonals dg, dg + 1 of 4 columns
+          uint32_t r0[4], r1[4];
           const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + dg * OZ_BN + half * OZ_DCOLS + c0;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                "=r"(r[14]), "=r"(r[15])
-              : "r"(ta));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3])
+                       : "r"(ta));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3])
+                       : "r"(ta + OZ_BN));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc64[c0 + j] = fma(w, (double)__uint_as_float(r[j]), acc64[c0 + j]);
+          for (int j = 0; j < 4; ++j) {
+            const long long x0 = __float2int_rn(__uint_as_float(r0[j]));   // exact: integers < 2^24
+            const long long x1 = __float2int_rn(__uint_as_float(r1[j]));
+            // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)), d >= 3 in b
+            if (dg == 0) H[c0 + j] += x0 * (1ll << 17) + x1 * (1ll << 10);
+            else if (dg == 2) { H[c0 + j] += x0 * (1ll << 3); b[j] += x1 * (1ll << 28); }
+            else b[j] += x0 * (1ll << (49 - OZ_BITS * dg)) + x1 * (1ll << (42 - OZ_BITS * dg));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {   // (H, L) += b with the carry out of the low word
+          const unsigned int lw = (unsigned int)b[j];
+          const unsigned int ln = L[c0 + j] + lw;
+          H[c0 + j] += (b[j] >> 32) + (ln < lw ? 1 : 0);
+          L[c0 + j] = ln;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -385,7 +407,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
 #pragma unroll
           for (int j = 0; j < OZ_DCOLS; ++j) {
             if (col0 + j < P.N) {
-              const double tv = acc64[j] * sr * scn[j];
+              // T = H 2^-31 + L 2^-63 (exact products, one rounding)
+              const double tv = fma((double)L[j], 0x1p-63, (double)H[j] * 0x1p-31) * sr * scn[j];
               c64 o;
               if (v == 0) {
                 o = make_double2(0.0, 0.0);
@@ -400,10 +423,11 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
               o.y = fma(ki, tv, o.y);
               crow[j] = o;
             }
+            if ((j & 3) == 3) asm volatile("" ::: "memory");   // keep the loads of later columns below
           }
         }
 #pragma unroll
-        for (int j = 0; j < OZ_DCOLS; ++j) acc64[j] = 0.0;
+        for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
       }
     }
   }
