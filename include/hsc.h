@@ -129,7 +129,7 @@ int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
  * schedule and workspace (rebuilt by the next solve). HSC_OPT_LEAF is read-only (the leaf_max of
  * the last hsc_analyze). */
 typedef enum {
-  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 64)                   */
+  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 32)                   */
   HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
   HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
   HSC_OPT_LEAF = 4,           /* read only                                                      */

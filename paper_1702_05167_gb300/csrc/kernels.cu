@@ -6,7 +6,11 @@
 //   * the anti-Hermitian completion of the lesser fold (Algorithm 2),
 //   * gathers of G_UU and P_UU from the ancestors' stored blocks (Algorithms 1-2, downward pass),
 //   * scatter of diag G^r, diag G^< and requested entries to user order.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hsc {
 namespace {
@@ -201,6 +205,119 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
     int t = idx / w, c = idx % w;
     R[(int64_t)t * n + k0 + c] = make_double2(t == c ? 1.0 : 0.0, 0.0);
   }
+}
+
+// The same panel step spread over a cluster of CS CTAs (CS = 2, 4) when a level has too few
+// (matrix, energy) pairs to fill the GPU: CTA q of the cluster owns the rows r with
+// (r / GJ_THREADS) % CS == q. Per column: each CTA publishes its best pivot candidate; after a cluster
+// barrier every CTA reads all candidates from distributed shared memory and takes the same pivot
+// (largest |re|+|im|, then smallest row: the single-CTA choice); every CTA reads rows j and p and
+// forms the scaled pivot row; after a second barrier the owners write rows j and p; each CTA
+// eliminates its own rows; a third barrier closes the column. The arithmetic of every row is the
+// single-CTA kernel's, so the results are bitwise identical. Cluster barriers are hardware barriers
+// that every thread of every CTA reaches the same number of times.
+template <int CS>
+__global__ void __launch_bounds__(GJ_THREADS)
+k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_es, c64* Mt,
+              c64* Rt, int64_t t_es, int k0, int nb, int* flag) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const GJProb P = probs[blockIdx.x / CS];
+  const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
+  if (k0 >= n) return;   // uniform over the cluster
+  const int w = min(nb, n - k0);
+  c64* A = F + e * f_es + P.off;
+  int32_t* pv = piv + e * piv_es + P.piv_off;
+  __shared__ double s_v[GJ_THREADS / 32];
+  __shared__ int s_i[GJ_THREADS / 32];
+  __shared__ double s_cbest;   // this CTA's candidate, read by the whole cluster
+  __shared__ int s_cidx;
+  __shared__ int s_p;
+  __shared__ c64 s_inv;
+  __shared__ c64 s_pr[64], s_old[64];   // scaled new row j, old row j (panel width <= 64)
+  auto owner = [&](int r) { return (r / GJ_THREADS) % CS; };
+  const int r_first = q * GJ_THREADS + tid, r_step = CS * GJ_THREADS;
+  for (int j = k0; j < k0 + w; ++j) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = r_first; r < n; r += r_step) {
+      if (r < j) continue;
+      c64 v = A[(int64_t)r * ld + j];
+      double a = fabs(v.x) + fabs(v.y);
+      if (a > best) { best = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { s_v[tid >> 5] = best; s_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = s_v[0];
+      int ix = s_i[0];
+      for (int k = 1; k < GJ_THREADS / 32; ++k)
+        if (s_v[k] > b || (s_v[k] == b && s_i[k] < ix)) { b = s_v[k]; ix = s_i[k]; }
+      s_cbest = b;
+      s_cidx = ix;
+    }
+    cluster.sync();   // 1: every candidate published
+    if (tid == 0) {
+      double b = -1.0;
+      int ix = n;
+      for (int k = 0; k < CS; ++k) {
+        const double ob = *cluster.map_shared_rank(&s_cbest, k);
+        const int oi = *cluster.map_shared_rank(&s_cidx, k);
+        if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
+      }
+      if (ix >= n) ix = j;
+      s_p = ix;
+      if (q == 0) pv[j] = ix;
+      c64 d = A[(int64_t)ix * ld + j];
+      if (d.x == 0.0 && d.y == 0.0) {
+        if (q == 0) atomicExch(flag, 1);
+        d = make_double2(1.0, 0.0);
+      }
+      s_inv = crecip(d);
+    }
+    __syncthreads();
+    const int p = s_p;
+    const c64 inv = s_inv;
+    for (int c = tid; c < w; c += GJ_THREADS) {
+      const c64 a = A[(int64_t)p * ld + k0 + c];   // becomes row j
+      s_old[c] = A[(int64_t)j * ld + k0 + c];      // becomes row p
+      s_pr[c] = (k0 + c == j) ? inv : cmul(a, inv);
+    }
+    cluster.sync();   // 2: rows j and p read everywhere before their owners overwrite them
+    if (owner(j) == q)
+      for (int c = tid; c < w; c += GJ_THREADS) A[(int64_t)j * ld + k0 + c] = s_pr[c];
+    if (p != j && owner(p) == q)
+      for (int c = tid; c < w; c += GJ_THREADS) A[(int64_t)p * ld + k0 + c] = s_old[c];
+    __syncthreads();
+    for (int r = r_first; r < n; r += r_step) {
+      if (r == j) continue;
+      c64* row = A + (int64_t)r * ld;
+      const c64 f = row[j];
+      for (int c = 0; c < w; ++c) {
+        if (k0 + c == j) continue;
+        row[k0 + c] = csub(row[k0 + c], cmul(f, s_pr[c]));
+      }
+      row[j] = cneg(cmul(f, inv));
+    }
+    cluster.sync();   // 3: the column is complete in every CTA
+  }
+  c64* M = Mt + e * t_es + P.mt_off;
+  c64* R = Rt + e * t_es + P.rt_off;
+  for (int r = r_first; r < n; r += r_step)
+    for (int c = 0; c < w; ++c) {
+      M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
+      A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
+    }
+  if (q == 0)
+    for (int idx = tid; idx < w * w; idx += GJ_THREADS) {
+      int t = idx / w, c = idx % w;
+      R[(int64_t)t * n + k0 + c] = make_double2(t == c ? 1.0 : 0.0, 0.0);
+    }
 }
 
 // apply the panel's row swaps to every column outside the panel and copy its pivot rows to R
@@ -456,9 +573,32 @@ cudaError_t launch_residual(int64_t n, const int64_t* rowptr, const c64* hval, c
 
 cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es, int32_t* piv,
                             int64_t piv_es, c64* Mt, c64* Rt, int64_t t_es, int k0, int nb, int ne,
-                            int* flag, cudaStream_t s) {
-  k_gj_panel<<<dim3(nmat, ne), GJ_THREADS, 0, s>>>(probs, F, f_es, piv, piv_es, Mt, Rt, t_es, k0, nb, flag);
-  return cudaGetLastError();
+                            int* flag, cudaStream_t s, int cluster) {
+  if (cluster <= 0) {   // clusters of 2 or 4 CTAs where the (matrix, energy) pairs leave SMs idle
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long pairs = (long long)nmat * ne;
+    cluster = pairs >= sms ? 1 : (2 * pairs >= sms ? 2 : 4);
+  }
+  if (cluster == 1) {
+    k_gj_panel<<<dim3(nmat, ne), GJ_THREADS, 0, s>>>(probs, F, f_es, piv, piv_es, Mt, Rt, t_es, k0, nb, flag);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nmat * cluster, ne);
+  cfg.blockDim = dim3(GJ_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cluster == 2)
+    return cudaLaunchKernelEx(&cfg, k_gj_panel_cl<2>, probs, F, f_es, piv, piv_es, Mt, Rt, t_es, k0, nb, flag);
+  return cudaLaunchKernelEx(&cfg, k_gj_panel_cl<4>, probs, F, f_es, piv, piv_es, Mt, Rt, t_es, k0, nb, flag);
 }
 
 cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,

@@ -15,7 +15,7 @@ cudaError_t launch_add_a(const LevelCluster* lc, int nl, int64_t max_h, int max_
                          c64* F, c64* L, int64_t aug_es, int ne, cudaStream_t s);
 cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es, int32_t* piv,
                             int64_t piv_es, c64* Mt, c64* Rt, int64_t t_es, int k0, int nb, int ne,
-                            int* flag, cudaStream_t s);
+                            int* flag, cudaStream_t s, int cluster = 1);
 cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
                            const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
                            int ne, cudaStream_t s);

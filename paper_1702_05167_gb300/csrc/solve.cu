@@ -78,11 +78,12 @@ struct DeviceState {
   uint64_t gen = ++g_generation;
   Prof prof;
   bool planned = false;
-  int nb = 64;                       // Gauss-Jordan panel width
+  int nb = 32;                       // Gauss-Jordan panel width
   int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
   bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
   bool four_products = false;        // FP64 engine: 4 real products per complex product (else 3M)
   int fp64_engine = 0;               // 0 cost model, 1 FP64 pipe only, 2 emulation wherever K > 0
+  int gj_cluster = 0;                // Gauss-Jordan panel: CTAs per (matrix, energy), 0 = by occupancy
   // energy-independent device arrays
   ClusterGlobal* cg = nullptr;
   LevelCluster* lcs = nullptr;
@@ -177,12 +178,14 @@ cudaError_t upload(DeviceState* d, T** dst, const std::vector<T>& v) {
 
 constexpr int TILE = 64;
 
-// Per-SM cost model of the two FP64-accurate engines in FP64-pipe operations (DFMA equivalents):
-// the FP64 pipe does 3 (4) K DFMA per element of a 64x64 tile; the emulation does, per 128x64 tile
-// and real product, 8 FP64 drains per 128 K values, 36 MMAs of 128x64x16 per 16 K values (about
-// 68 DFMA-times each: ~36 clocks at one MMA-tile per clock, 1.9 DFMA per clock and SM) and the
-// epilogue, plus the slicing pass (about 9 DFMA-times per operand element at HBM speed).
-constexpr double OZ_MMA_DFMA = 68.0, OZ_PACK_DFMA = 9.0;
+// Per-SM cost model of the two FP64-accurate engines in FP64-pipe operations (DFMA equivalents,
+// 1.9 DFMA per clock and SM): the FP64 pipe does 3 (4) K DFMA per element of a 64x64 tile; the
+// emulation does, per 128x64 tile and real product, one integer drain per 128 K values (8 F2I and
+// ~20 integer operations per element, ~0.8 clocks), 36 MMAs of 128x64x16 per 16 K values (~36
+// clocks each), an FP64 epilogue of ~7 operations per element, plus the slicing pass (about 9
+// DFMA-times per operand element at HBM speed).
+constexpr double OZ_DRAIN_DFMA = 8192 * 0.8 * 1.9, OZ_MMA_DFMA = 68.0, OZ_EPI_DFMA = 8192 * 7.0,
+                 OZ_PACK_DFMA = 9.0;
 
 struct GemmList {
   std::vector<GemmProb>& all;      // 64x64-tile problem lists
@@ -228,7 +231,8 @@ struct GemmList {
     const double tz = (double)((M + TILE - 1) / TILE) * p.tiles_n * TILE * TILE;
     cost_z += tz * 3.0 * K;
     const double nt = tilesoz - t0;
-    cost_oz += nt * 3.0 * (std::ceil(K / 128.0) * 8 * 8192 + std::ceil(K / 16.0) * 36 * OZ_MMA_DFMA + 4 * 8192) +
+    cost_oz += nt * 3.0 * (std::ceil(K / 128.0) * OZ_DRAIN_DFMA + std::ceil(K / 16.0) * 36 * OZ_MMA_DFMA +
+                           OZ_EPI_DFMA) +
                ((double)M * K + (double)K * N) * OZ_PACK_DFMA;
     all.push_back(p);
     all128.push_back(q);
@@ -743,7 +747,7 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       const int k0 = (int)st * d->nb;
       LAUNCH(K_GJ_PANEL, 1, 0.0, 0.0,
              launch_gj_panel(gp, U.nmat, d->F, d->aug_es, d->piv, d->piv_es, d->GJT, d->GJT,
-                             d->gjt_es, k0, d->nb, ne, d->flag, s));
+                             d->gjt_es, k0, d->nb, ne, d->flag, s, d->gj_cluster));
       LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
              launch_gj_swap(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
                             d->gjt_es, k0, d->nb, ne, s));
@@ -867,6 +871,8 @@ int new_state(hsc_ctx* h) {
   h->dev->four_products = h->opt_4m != 0;
   h->dev->fp64_engine = h->opt_fp64_engine;
   if (const char* v = getenv("HSC_FP64_ENGINE")) h->dev->fp64_engine = atoi(v);
+  if (const char* v = getenv("HSC_GJ_CLUSTER")) h->dev->gj_cluster = atoi(v);
+  if (h->dev->gj_cluster != 1 && h->dev->gj_cluster != 2 && h->dev->gj_cluster != 4) h->dev->gj_cluster = 0;
   if (const char* v = getenv("HSC_FP64_LEVELS")) h->dev->fp64_levels = atoi(v);
   if (const char* v = getenv("HSC_MIXED_GJ_FP64")) h->dev->gj_fp64 = atoi(v) != 0;
   if (const char* v = getenv("HSC_TC_PACK")) h->dev->use_pack = atoi(v) != 0;
@@ -1572,7 +1578,7 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
     if (l < maxdim) leaves.push_back(l);
   if (leaves.empty()) leaves.push_back(h->leaf_max > 0 ? h->leaf_max : 4);
   double best = 1e300;
-  int best_leaf = leaves[0], best_nb = 64, tried = 0;
+  int best_leaf = leaves[0], best_nb = 32, tried = 0;
   (void)ncs;
   for (int leaf : leaves)
     for (int nb : {16, 32, 64}) {

@@ -169,7 +169,7 @@ def test_options_round_trip_and_reject_bad_values():
     dev = W.cubic_device((4, 4, 4), seed=0)
     h = _handle(dev)
     hsc.hsc_analyze(h, 2)
-    assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 64
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 32
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF) == 2
     hsc.hsc_set_option(h, hsc.HSC_OPT_GJ_PANEL, 8)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 8

@@ -376,6 +376,7 @@ def test_resolve_on_alternate_trees():
     for digits in (0, 6):
         s = hsc.Solver(dev, 4)
         hsc.hsc_set_option(s.h, hsc.HSC_OPT_RESOLVE_DIGITS, digits)
+        hsc.hsc_set_option(s.h, hsc.HSC_OPT_GJ_PANEL, 16)   # the rounding this set was examined with
         out[digits] = s.solve(E, 1e-6, sr, sl, pairs=pairs)
         out[(digits, "r")] = hsc.hsc_residual(s.h, len(E))
         if digits:
@@ -400,3 +401,22 @@ def test_resolve_on_alternate_trees():
     # energies that were not re-solved are bit-identical
     same = out[(0, "r")] <= 1e-6
     assert np.array_equal(out[6][0][same], out[0][0][same])
+
+
+@pytest.mark.parametrize("cluster", ["2", "4"])
+def test_gauss_jordan_cluster_panels_are_bitwise_identical(cluster, monkeypatch):
+    """The Gauss-Jordan panel step spread over a cluster of 2 or 4 CTAs per (matrix, energy) takes
+    the same pivots and does the same arithmetic per row as the single-CTA kernel: the solve's
+    outputs must be bit-identical (few energies, so the automatic choice would use clusters)."""
+    dev = W.cubic_device((12, 11, 10), W=1.0, seed=6)
+    E = np.array([-1.3, 0.2, 2.4])
+    sr, sl = W.self_energies(dev, len(E), (1.0, 0.4))
+    out = {}
+    for c in ("1", cluster):
+        monkeypatch.setenv("HSC_GJ_CLUSTER", c)
+        s = hsc.Solver(dev, 5)
+        hsc.hsc_set_option(s.h, hsc.HSC_OPT_GJ_PANEL, 16)
+        out[c] = s.solve(E, ETA_WELL, sr, sl, pairs=W.plane_pairs(dev, 5))
+        s.close()
+    for a, b in zip(out["1"], out[cluster]):
+        assert np.array_equal(a, b)
