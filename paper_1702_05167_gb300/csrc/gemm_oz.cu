@@ -23,7 +23,8 @@
 //     2^-53.1 from the dropped diagonals d >= 10 (7 * 127^2 * 2^-70 for d = 10, less beyond).
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
 // op(A) (all 8 slices, 32 KB) and a 64 x 16 block of op(B)^T (16 KB) in the K-major core-matrix
-// layout the MMA reads, for each of the three real operands (re, im, re + im).
+// layout the MMA reads, for each of the three real operands (re, im, re + im), reading each complex
+// element once per pass and writing 16-byte runs.
 // Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
 // real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
 // counts), warp 1 issues the 36 MMAs of each K step, warps 2-9 drain the accumulators every 8 K steps
@@ -104,15 +105,11 @@ __device__ __forceinline__ int oz_expo(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// real operand v (0: re, 1: im, 2: re + im) of a complex value after the op's conjugation
-template <bool CONJ>
-__device__ __forceinline__ double oz_part(c64 x, int v) {
-  const double im = CONJ ? -x.y : x.y;
-  return v == 0 ? x.x : (v == 1 ? im : x.x + im);
-}
-
-// One CTA per (problem, side, real operand, tile): side A = 128 rows of op(A), side B = 64 rows of
-// op(B)^T (columns of op(B)). Layout per problem and energy (BF16 values):
+// One CTA per (problem, side, tile): side A = 128 rows of op(A), side B = 64 rows of op(B)^T
+// (columns of op(B)), all three real operands (re, im, re + im) from one read of each complex
+// element per pass. A thread task is (row, run of 8 consecutive k): its slices of one plane are 16
+// contiguous bytes of the core-matrix layout, written as one 16-byte store. Layout per problem and
+// energy (BF16 values):
 //   A images at pa: [v][tile_m][kstep][slice][128 x 16],  B images at pb: [v][tile_n][kstep][slice][64 x 16];
 //   scales (doubles) at sa: [v][tiles_m * 128],  at sb: [v][tiles_n * 64].
 template <int OPA, int OPB>
@@ -127,77 +124,97 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
     else hi = mid - 1;
   }
   const GemmProb P = g.probs[lo];
-  int b = blk - P.pack_start;
-  const bool isA = b < 3 * P.tiles_m;
-  if (!isA) b -= 3 * P.tiles_m;
-  const int ntile = isA ? P.tiles_m : P.tiles_n;
-  const int v = b / ntile, tile = b % ntile;
+  int tile = blk - P.pack_start;
+  const bool isA = tile < P.tiles_m;
+  if (!isA) tile -= P.tiles_m;
   const int rows = isA ? OZ_BM : OZ_BN;
   const int row0 = tile * rows;
   const int nrow = isA ? P.M : P.N;
-  const int K = P.K, ks = P.ksteps, Kp = ks * OZ_BK;
+  const int K = P.K, ks = P.ksteps;
   const c64* X = reinterpret_cast<const c64*>(isA ? g.A : g.B) + e * (isA ? g.a_es : g.b_es) + (isA ? P.a : P.b);
   const int ld = isA ? P.lda : P.ldb;
   // row r of op(A) (or of op(B)^T) is contiguous in memory for op(A) in {N, C} and op(B) in {T, H}
   const bool krun = isA ? (OPA == OP_N || OPA == OP_C) : (OPB == OP_T || OPB == OP_H);
   const bool conj = isA ? (OPA == OP_C || OPA == OP_H) : (OPB == OP_C || OPB == OP_H);
-  auto value = [&](int r, int k) -> double {
-    const c64 x = krun ? X[(int64_t)r * ld + k] : X[(int64_t)k * ld + r];
-    return conj ? oz_part<true>(x, v) : oz_part<false>(x, v);
+  auto load = [&](int r, int k) -> c64 {   // element (r, k) after the op's conjugation, 0 outside
+    if (row0 + r >= nrow || k >= K) return make_double2(0.0, 0.0);
+    c64 x = krun ? X[(int64_t)(row0 + r) * ld + k] : X[(int64_t)k * ld + row0 + r];
+    if (conj) x.y = -x.y;
+    return x;
   };
-  uint16_t* dst = slices + e * slice_es +
-                  (isA ? P.pa + ((int64_t)v * P.tiles_m + tile) * ks * OZ_ABLK
-                       : P.pb + ((int64_t)v * P.tiles_n + tile) * ks * OZ_BBLK);
-  double* sc = scales + e * scale_es + (isA ? P.sa + (int64_t)v * P.tiles_m * OZ_BM
-                                            : P.sb + (int64_t)v * P.tiles_n * OZ_BN) + row0;
-  __shared__ int s_e[OZ_BM];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int r = tid; r < rows; r += OZP_THREADS) s_e[r] = 0;
+  const int64_t blkv = isA ? OZ_ABLK : OZ_BBLK;
+  const int64_t vstride = (int64_t)(isA ? P.tiles_m : P.tiles_n) * ks * blkv;   // between real operands
+  uint16_t* dst = slices + e * slice_es + (isA ? P.pa + (int64_t)tile * ks * OZ_ABLK : P.pb + (int64_t)tile * ks * OZ_BBLK);
+  double* sc = scales + e * scale_es + (isA ? P.sa : P.sb) + row0;
+  const int64_t sstride = (int64_t)(isA ? P.tiles_m * OZ_BM : P.tiles_n * OZ_BN);
+  __shared__ int s_e[3][OZ_BM];
+  const int tid = threadIdx.x;
+  for (int r = tid; r < 3 * OZ_BM; r += OZP_THREADS) s_e[r / OZ_BM][r % OZ_BM] = 0;
   __syncthreads();
-  // largest biased exponent per row (0 for a row of zeros)
-  if (krun) {
-    for (int r = warp; r < rows; r += OZP_THREADS / 32) {
-      int ex = 0;
-      if (row0 + r < nrow)
-        for (int k = lane; k < K; k += 32) ex = max(ex, oz_expo(value(row0 + r, k)));
-      ex = (int)__reduce_max_sync(0xffffffffu, (unsigned)ex);
-      if (lane == 0) s_e[r] = ex;
+  const int ngrp = ks * (OZ_BK / 8);        // runs of 8 k per row
+  const int ntask = rows * ngrp;            // lanes run over rows: coalesced for either orientation
+  // pass 1: largest biased exponent per row and real operand (0 for a row of zeros)
+  for (int t = tid; t < ntask; t += OZP_THREADS) {
+    const int r = t % rows, k0 = (t / rows) * 8;
+    if (row0 + r >= nrow || k0 >= K) continue;
+    int e0 = 0, e1 = 0, e2 = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const c64 x = load(r, k0 + q);
+      e0 = max(e0, oz_expo(x.x));
+      e1 = max(e1, oz_expo(x.y));
+      e2 = max(e2, oz_expo(x.x + x.y));
     }
-  } else {
-    const int phases = OZP_THREADS / rows;
-    const int r = tid % rows, ph = tid / rows;
-    int ex = 0;
-    if (row0 + r < nrow)
-      for (int k = ph; k < K; k += phases) ex = max(ex, oz_expo(value(row0 + r, k)));
-    atomicMax(&s_e[r], ex);
+    if (e0) atomicMax(&s_e[0][r], e0);
+    if (e1) atomicMax(&s_e[1][r], e1);
+    if (e2) atomicMax(&s_e[2][r], e2);
   }
   __syncthreads();
   // sigma = 2^(E - 1022) > |x| for every x of the row with biased exponent <= E
-  for (int r = tid; r < rows; r += OZP_THREADS) sc[r] = s_e[r] > 0 ? ldexp(1.0, s_e[r] - 1022) : 0.0;
-  const int plane = rows * OZ_BK;
-  const int64_t blkv = isA ? OZ_ABLK : OZ_BBLK;
-  const int total = rows * Kp;
-  for (int i = tid; i < total; i += OZP_THREADS) {
-    const int r = krun ? i / Kp : i % rows;
-    const int k = krun ? i % Kp : i / rows;
-    const int gr = row0 + r;
-    const double x = (gr < nrow && k < K) ? value(gr, k) : 0.0;
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    // m = floor(|x| / sigma * 2^56): |x| = mant 2^(ex - 1075), sigma = 2^(E - 1022), so the 53-bit
-    // significand moves right by E - ex + 52 - 56 + 1 (a left shift of at most 3 when ex = E)
-    unsigned long long m = 0;
-    const int shift = s_e[r] - ex + (52 - OZ_FRAC + 1);
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    if (ex > 0 && shift < 64) m = shift >= 0 ? mant >> shift : mant << (-shift);
-    const uint32_t sgn = (uint32_t)(bits >> 63) << 15;
-    uint16_t* o = dst + (int64_t)(k / OZ_BK) * blkv + oz_cidx(r, k % OZ_BK);
+  for (int i = tid; i < 3 * rows; i += OZP_THREADS) {
+    const int v = i / rows, r = i % rows;
+    sc[v * sstride + r] = s_e[v][r] > 0 ? ldexp(1.0, s_e[v][r] - 1022) : 0.0;
+  }
+  // pass 2: slices, 8 consecutive k of one row per task
+  for (int t = tid; t < ntask; t += OZP_THREADS) {
+    const int r = t % rows, k0 = (t / rows) * 8;
+    c64 x[8];
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const uint32_t t = (uint32_t)(m >> (OZ_FRAC - OZ_BITS * (s + 1))) & 127u;
-      // t as an FP32 value (exact: t < 2^23), whose upper half is its exact BF16 encoding
-      const float f = __uint_as_float(0x4B000000u | t) - 8388608.0f;
-      o[s * plane] = (uint16_t)((__float_as_uint(f) >> 16) | sgn);
+    for (int q = 0; q < 8; ++q) x[q] = load(r, k0 + q);
+    uint16_t* o = dst + (int64_t)(k0 / OZ_BK) * blkv + oz_cidx(r, k0 % OZ_BK);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      unsigned long long m[8];
+      uint32_t sg[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double val = v == 0 ? x[q].x : (v == 1 ? x[q].y : x[q].x + x[q].y);
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(val);
+        const int ex = (int)((bits >> 52) & 0x7FF);
+        // m = floor(|x| / sigma * 2^56): |x| = mant 2^(ex - 1075), sigma = 2^(E - 1022), so the 53-bit
+        // significand moves right by E - ex + 52 - 56 + 1 (a left shift of at most 3 when ex = E)
+        const int shift = s_e[v][r] - ex + (52 - OZ_FRAC + 1);
+        const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        m[q] = (ex > 0 && shift < 64) ? (shift >= 0 ? mant >> shift : mant << (-shift)) : 0ull;
+        sg[q] = (uint32_t)(bits >> 63) << 15;
+      }
+#pragma unroll
+      for (int sl = 0; sl < OZ_S; ++sl) {
+        uint32_t h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t tq = (uint32_t)(m[q] >> (OZ_FRAC - OZ_BITS * (sl + 1))) & 127u;
+          // tq as an FP32 value (exact: tq < 2^23), whose upper half is its exact BF16 encoding
+          const float f = __uint_as_float(0x4B000000u | tq) - 8388608.0f;
+          h[q] = (__float_as_uint(f) >> 16) | sg[q];
+        }
+        uint4 w;
+        w.x = h[0] | (h[1] << 16);
+        w.y = h[2] | (h[3] << 16);
+        w.z = h[4] | (h[5] << 16);
+        w.w = h[6] | (h[7] << 16);
+        *reinterpret_cast<uint4*>(o + v * vstride + sl * (rows * OZ_BK)) = w;
+      }
     }
   }
 }
@@ -449,7 +466,7 @@ void oz_layout(GemmProb& p, int& pack_blocks, int& tiles, int64_t& slice_vals, i
   p.tile_start = tiles;
   tiles += p.tiles_m * p.tiles_n;
   p.pack_start = pack_blocks;
-  pack_blocks += p.ksteps > 0 ? 3 * (p.tiles_m + p.tiles_n) : 0;
+  pack_blocks += p.ksteps > 0 ? p.tiles_m + p.tiles_n : 0;
   p.pa = slice_vals;
   p.pb = slice_vals + 3LL * p.tiles_m * p.ksteps * OZ_ABLK;
   slice_vals = p.pb + 3LL * p.tiles_n * p.ksteps * OZ_BBLK;
