@@ -82,6 +82,40 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, unsigned 
   }
 }
 
+// The double nearest to (H 2^32 + L) 2^es (H 2^32 + L: a signed 96-bit integer), built on the
+// integer pipe: normalise by the leading bit, round to 53 bits (ties away from zero), place the
+// exponent. Falls back to FP64 arithmetic when the result would leave the normal range.
+__device__ __forceinline__ double oz_fix_to_double(long long H, unsigned int L, int es) {
+  if (H == 0 && L == 0u) return 0.0;
+  const bool neg = H < 0;
+  unsigned long long mh = (unsigned long long)H;
+  unsigned int ml = L;
+  if (neg) {   // two's complement of the 96-bit value
+    ml = ~L + 1u;
+    mh = ~mh + (ml == 0u ? 1ull : 0ull);
+  }
+  unsigned long long top;   // the 64 bits below and including the leading one
+  int lead;                 // position of the leading one in the 96-bit magnitude
+  if (mh != 0ull) {
+    const int lz = __clzll((long long)mh);
+    top = lz == 0 ? mh : ((mh << lz) | (lz <= 32 ? (((unsigned long long)ml << lz) >> 32)
+                                                 : ((unsigned long long)ml << (lz - 32))));
+    lead = 95 - lz;
+  } else {
+    const int lz = __clz((int)ml);
+    top = (unsigned long long)ml << (32 + lz);
+    lead = 31 - lz;
+  }
+  unsigned long long m = (top >> 11) + ((top >> 10) & 1ull);   // 53 bits, rounded
+  int ex = lead + es;
+  if (m >> 53) { m >>= 1; ++ex; }
+  const int biased = ex + 1023;
+  if (biased < 1 || biased > 2046)   // not representable as a normal double: the slow, exact way
+    return ldexp(fma((double)L, 0x1p-32, (double)H), es + 32);
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
+                                          ((unsigned long long)biased << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
 // element (r, k) of a rows x 16 K-major BF16 block: core matrices of 8 rows x 16 B (8 values); the
 // two K-adjacent core matrices are 128 B apart, adjacent 8-row groups 256 B apart
 __device__ __forceinline__ int oz_cidx(int r, int k) {
@@ -419,13 +453,15 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
         if (row < P.M) {
           const double sr = scales[e * scale_es + P.sa + (int64_t)v * P.tiles_m * OZ_BM + row];
           const double* scn = scales + e * scale_es + P.sb + (int64_t)v * P.tiles_n * OZ_BN + col0;   // col0 includes the tile
+          // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
+          const int er = oz_expo(sr) - 1023 - 63;
           c64* crow = C + (int64_t)row * P.ldc + col0;
           const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
 #pragma unroll
           for (int j = 0; j < OZ_DCOLS; ++j) {
             if (col0 + j < P.N) {
-              // T = H 2^-31 + L 2^-63 (exact products, one rounding)
-              const double tv = fma((double)L[j], 0x1p-63, (double)H[j] * 0x1p-31) * sr * scn[j];
+              // T sigma tau = (H 2^32 + L) 2^(-63 + log2 sigma + log2 tau), rounded once
+              const double tv = oz_fix_to_double(H[j], L[j], er + oz_expo(scn[j]) - 1023);
               c64 o;
               if (v == 0) {
                 o = make_double2(0.0, 0.0);
