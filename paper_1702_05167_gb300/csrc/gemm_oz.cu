@@ -27,7 +27,8 @@
 // element once per pass and writing 16-byte runs.
 // Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
 // real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
-// counts), warp 1 issues the 36 MMAs of each K step, warps 2-9 drain the accumulators every 8 K steps
+// counts), warp 1 issues the 36 MMAs of each K step into the 8 diagonal accumulators (512 TMEM
+// columns), warps 2-17 drain them every 8 K steps (16 columns of exact state per thread)
 // and, after the last chunk of a real product, add its share to C (read-modify-write by the owning
 // thread, so C may alias D). Every mbarrier wait is bounded; on expiry the kernel raises the flag,
 // waits (bounded) for its own copies, frees tensor memory and returns.
@@ -49,15 +50,18 @@ constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (a
 constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_DRAIN = 8;              // K steps per drain (128 K values)
-constexpr uint32_t OZ_TMEM_COLS = 512;   // 8 accumulators x 64 columns
+constexpr int OZ_ACC = OZ_ND * OZ_BN;     // TMEM columns of one set of accumulators
+constexpr uint32_t OZ_TMEM_COLS = 512;
+constexpr int OZ_NBUF = 2 * OZ_ACC <= (int)OZ_TMEM_COLS ? 2 : 1;   // sets (2: drain overlaps MMAs)
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
-constexpr int OZ_DRAIN_WARPS = 8;      // two per TMEM lane quadrant, 32 columns each
-constexpr int OZ_DCOLS = OZ_BN / 2;
+constexpr int OZ_DRAIN_WARPS = 16;     // four per TMEM lane quadrant
+constexpr int OZ_DCOLS = OZ_BN / (OZ_DRAIN_WARPS / 4);   // columns of exact state per drain thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;
 constexpr int OZP_THREADS = 256;
 
-static_assert(OZ_ND * OZ_BN <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
+static_assert(OZ_NBUF * OZ_ACC <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
 static_assert((long long)OZ_S * 127 * 127 * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
+static_assert(OZ_ND == 8 && OZ_BITS == 7, "the drain's diagonal weights assume 8 diagonals of 7 bits");
 
 __device__ __forceinline__ uint32_t oz_su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -258,8 +262,8 @@ struct __align__(128) OzSmem {
   uint16_t b[OZ_STAGES][OZ_BBLK];
   unsigned long long full[OZ_STAGES];
   unsigned long long empty[OZ_STAGES];
-  unsigned long long acc_full;    // MMA -> drain: a chunk of K steps is in the accumulators
-  unsigned long long acc_empty;   // drain -> MMA: accumulators read
+  unsigned long long acc_full[2];    // MMA -> drain: a chunk of K steps is in accumulator set b
+  unsigned long long acc_empty[2];   // drain -> MMA: set b read
   uint32_t tmem;
   int abort;
 };
@@ -305,8 +309,10 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.acc_full)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(&sm.acc_empty)), "r"(OZ_DRAIN_WARPS));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&sm.acc_full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(&sm.acc_empty[b])), "r"(OZ_DRAIN_WARPS));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     sm.abort = 0;
   }
@@ -344,7 +350,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
     if (lane == 0) {   // MMA issuer
       bool ok = true;
       for (int c = 0; c < 3 * nchunk && ok; ++c) {
-        if (c > 0 && !oz_wait(oz_su32(&sm.acc_empty), (uint32_t)((c - 1) & 1))) {
+        const int ab = c % OZ_NBUF;   // accumulator set of this chunk; its previous chunk was c - OZ_NBUF
+        if (c >= OZ_NBUF && !oz_wait(oz_su32(&sm.acc_empty[ab]), (uint32_t)((c / OZ_NBUF - 1) & 1))) {
           atomicExch(flag, 3);
           *abort_flag = 1;
           break;
@@ -368,21 +375,21 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
             for (int ri = 0; ri < OZ_S - si; ++ri) {   // s + r <= OZ_S + 1 (1-based slices)
               // the first MMA of a chunk into diagonal si + ri is the one with si = 0
               const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
-              oz_mma(tmem + (si + ri) * OZ_BN, oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)),
+              oz_mma(tmem + ab * OZ_ACC + (si + ri) * OZ_BN, oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)),
                      oz_desc(b0 + ri * (OZ_BN * OZ_BK * 2)), idesc, acc);
             }
           oz_commit(oz_su32(&sm.empty[st]));
         }
-        oz_commit(oz_su32(&sm.acc_full));   // also releases the drain warps after an abort
+        oz_commit(oz_su32(&sm.acc_full[ab]));   // also releases the drain warps after an abort
       }
     }
-  } else {   // warps 2-9: drain, TMEM lane quadrant = warp % 4, column half = (warp - 2) / 4
-    const int quad = warp & 3, half = (warp - 2) >> 2;
+  } else {   // warps 2..: drain, TMEM lane quadrant = warp % 4, column part = (warp - 2) / 4
+    const int quad = warp & 3, part = (warp - 2) >> 2;
     const int row = tm * OZ_BM + quad * 32 + lane;
     c64* C = reinterpret_cast<c64*>(g.C) + e * g.c_es + P.c;
     const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
     const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
-    const int col0 = tn * OZ_BN + half * OZ_DCOLS;
+    const int col0 = tn * OZ_BN + part * OZ_DCOLS;
     // exact running sum T 2^63 = H 2^32 + L of the chunks; |H| < nchunk 2^41.1, exact in FP64 for
     // nchunk < 2^11 (K < 262144)
     long long H[OZ_DCOLS];
@@ -400,7 +407,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       }
     }
     for (int c = 0; c < 3 * nchunk; ++c) {
-      bool got = oz_wait(oz_su32(&sm.acc_full), (uint32_t)(c & 1));
+      const int ab = c % OZ_NBUF;
+      bool got = oz_wait(oz_su32(&sm.acc_full[ab]), (uint32_t)((c / OZ_NBUF) & 1));
       got = __all_sync(0xffffffffu, got);   // warp-uniform before the .sync.aligned TMEM loads
       if (!got) {
         if (lane == 0) atomicExch(flag, 3);
@@ -409,42 +417,33 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int c0 = 0; c0 < OZ_DCOLS; c0 += 4) {
-        long long b[4];   // this chunk's diagonals 3..7 of 4 columns: sum v_d 2^(49 - 7 d) < 2^52.1
+      for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
+        // all 8 diagonals of 2 columns behind one wait
+        uint32_t r[OZ_ND][2];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ab * OZ_ACC + part * OZ_DCOLS + c0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = 0;
+        for (int dg = 0; dg < OZ_ND; ++dg)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+                       : "=r"(r[dg][0]), "=r"(r[dg][1])
+                       : "r"(ta + dg * OZ_BN));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int dg = 0; dg < OZ_ND; dg += 2) {   // diagonals dg, dg + 1 of 4 columns
-          uint32_t r0[4], r1[4];
-          const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + dg * OZ_BN + half * OZ_DCOLS + c0;
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3])
-                       : "r"(ta));
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3])
-                       : "r"(ta + OZ_BN));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int j = 0; j < 2; ++j) {
+          // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)); d >= 3 in
+          // b = sum v_d 2^(49 - 7 d) < 2^52.1, added to (H, L) with the carry out of the low word
+          long long x[OZ_ND];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const long long x0 = __float2int_rn(__uint_as_float(r0[j]));   // exact: integers < 2^24
-            const long long x1 = __float2int_rn(__uint_as_float(r1[j]));
-            // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)), d >= 3 in b
-            if (dg == 0) H[c0 + j] += x0 * (1ll << 17) + x1 * (1ll << 10);
-            else if (dg == 2) { H[c0 + j] += x0 * (1ll << 3); b[j] += x1 * (1ll << 28); }
-            else b[j] += x0 * (1ll << (49 - OZ_BITS * dg)) + x1 * (1ll << (42 - OZ_BITS * dg));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {   // (H, L) += b with the carry out of the low word
-          const unsigned int lw = (unsigned int)b[j];
+          for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
+          const long long b = x[3] * (1ll << 28) + x[4] * (1ll << 21) + x[5] * (1ll << 14) + x[6] * (1ll << 7) + x[7];
+          const unsigned int lw = (unsigned int)b;
           const unsigned int ln = L[c0 + j] + lw;
-          H[c0 + j] += (b[j] >> 32) + (ln < lw ? 1 : 0);
+          H[c0 + j] += x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32) + (ln < lw ? 1 : 0);
           L[c0 + j] = ln;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty)) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty[ab])) : "memory");
       const int v = c / nchunk;
       if (c % nchunk == nchunk - 1) {   // real product v complete: C += kappa_v T_v
         // kappa_0 = alpha (1 - i), kappa_1 = alpha (-1 - i), kappa_2 = alpha i
