@@ -17,8 +17,9 @@
 //     memory accumulator, exact for 128 K values (at most 8 pairs: 8 * 127^2 * 128 < 2^24); every
 //     128 K values the 8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe
 //     would otherwise bound the kernel), into the 96-bit integer T 2^63 = H 2^32 + L per element
-//     (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)); T = H 2^-31 + L 2^-63 once
-//     per product, the only rounding;
+//     (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)); once per product T sigma_i
+//     tau_j is rounded to the nearest double, also on the integer pipe (the scales are powers of
+//     two), the only rounding;
 //   * per K value the error is below 2^-52.8 sigma_i tau_j: 2 * 2^-56 from the truncation and
 //     2^-53.1 from the dropped diagonals d >= 10 (7 * 127^2 * 2^-70 for d = 10, less beyond).
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
