@@ -169,16 +169,11 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
     __syncthreads();
     const int p = s_p;
     const c64 inv = s_inv;
-    if (p != j)
-      for (int c = tid; c < w; c += GJ_THREADS) {
-        c64 t = A[(int64_t)j * ld + k0 + c];
-        A[(int64_t)j * ld + k0 + c] = A[(int64_t)p * ld + k0 + c];
-        A[(int64_t)p * ld + k0 + c] = t;
-      }
-    __syncthreads();
+    // swap rows j and p inside the panel and scale the new row j (each thread owns its columns)
     for (int c = tid; c < w; c += GJ_THREADS) {
-      int64_t o = (int64_t)j * ld + k0 + c;
-      A[o] = (k0 + c == j) ? inv : cmul(A[o], inv);
+      const c64 a = A[(int64_t)p * ld + k0 + c];
+      if (p != j) A[(int64_t)p * ld + k0 + c] = A[(int64_t)j * ld + k0 + c];
+      A[(int64_t)j * ld + k0 + c] = (k0 + c == j) ? inv : cmul(a, inv);
     }
     __syncthreads();
     for (int r = tid; r < n; r += GJ_THREADS) {
@@ -213,9 +208,12 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
 // barrier every CTA reads all candidates from distributed shared memory and takes the same pivot
 // (largest |re|+|im|, then smallest row: the single-CTA choice); every CTA reads rows j and p and
 // forms the scaled pivot row; after a second barrier the owners write rows j and p; each CTA
-// eliminates its own rows; a third barrier closes the column. The arithmetic of every row is the
-// single-CTA kernel's, so the results are bitwise identical. Cluster barriers are hardware barriers
-// that every thread of every CTA reaches the same number of times.
+// eliminates its own rows. No barrier closes the column: the next candidate search reads only the
+// CTA's own rows, the next cross-CTA reads of pivot rows follow the next column's first barrier
+// (release/acquire at cluster scope), and every read of another CTA's shared memory precedes the
+// column's second barrier. The arithmetic of every row is the single-CTA kernel's, so the results
+// are bitwise identical. Cluster barriers are hardware barriers that every thread of every CTA
+// reaches the same number of times.
 template <int CS>
 __global__ void __launch_bounds__(GJ_THREADS)
 k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_es, c64* Mt,
@@ -304,7 +302,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
       }
       row[j] = cneg(cmul(f, inv));
     }
-    cluster.sync();   // 3: the column is complete in every CTA
+    __syncthreads();   // this CTA's rows are complete before its next candidate search
   }
   c64* M = Mt + e * t_es + P.mt_off;
   c64* R = Rt + e * t_es + P.rt_off;
