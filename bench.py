@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the batch8 workload")
-    p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E", "batch8"],
+    p.add_argument("--energies", type=int, default=0,
+                   help="solve only this many of the workload's energies (every k-th; 0: all)")
+    p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E", "batch8", "wire"],
                    help="cubic32: the metric workload; cubic24x8E: 24^3 grid, 8 energies (a few GB, "
                         "for ncu captures)")
     return p.parse_args()
@@ -109,14 +111,19 @@ def dist():
     return ws, rank, local
 
 
-def workload(rank, ws, name="cubic32"):
+def workload(rank, ws, name="cubic32", n_energies=0):
     from paper_1702_05167_gb300 import workloads as W
     cfg = W.mid()
+    if name == "wire":   # 10 orbitals on 64 x 12 x 12 sites; leaves 4 (the cheapest tree: 6 TFLOP per energy)
+        cfg = dict(W.wire(), leaf=4, pairs=None)
     if name == "cubic24x8E":
         dev = W.cubic_device((24, 24, 24), t=-1.0, W=1.0, seed=0, gamma=0.5)
         cfg = dict(name="cubic_24x24x24_8E", dev=dev, energies=np.linspace(-5.5, 5.5, 8), eta=1e-6,
                    leaf=8, f=(1.0, 0.0), pairs=W.plane_pairs(dev, 11))
     from paper_1702_05167_gb300 import sharding
+    if n_energies and n_energies < len(cfg["energies"]):
+        step = len(cfg["energies"]) // n_energies
+        cfg["energies"] = cfg["energies"][::step][:n_energies]
     cfg["energies"] = sharding.interleaved_grid(cfg["energies"], rank, ws)
     return cfg
 
@@ -171,12 +178,14 @@ def run_hsc(args):
         tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dvc = torch.device("cuda", local)
-    cfg = workload(rank, ws, args.workload)
+    cfg = workload(rank, ws, args.workload, args.energies)
     dev = cfg["dev"]
     E = cfg["energies"]
     nE = len(E)
     sr, sl = W.self_energies(dev, nE, cfg["f"])
-    pairs = cfg["pairs"]
+    pairs = cfg.get("pairs")
+    if pairs is None:
+        pairs = np.zeros((0, 2), dtype=np.int32)
     solver = hsc.Solver(dev, cfg["leaf"])
     st = solver.stats
     h = solver.h
