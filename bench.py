@@ -231,6 +231,8 @@ def run_hsc(args):
     hsc.hsc_profile(h, False)
     growth = hsc.hsc_growth(h, nE)
     resid = hsc.hsc_residual(h, nE)
+    kq = 20   # the energy the CPU oracle checks; keep the timed step's outputs there (ogr etc. are reused)
+    timed_out = [t_.cpu().numpy().view(np.complex128)[kq].copy() for t_ in (ogr, ogl, pgr, pgl)]
     if ws > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dvc)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -355,8 +357,8 @@ def run_hsc(args):
     if not args.no_tune:
         cache = os.environ.get("HSC_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "hsc_tune.jsonl"))
         st_t = hsc.Solver(dev, cfg["leaf"])
-        r = hsc.hsc_tune(st_t.h, E[[10, 40]], cfg["eta"], sr[[10, 40]], sl[[10, 40]],
-                         cache_path=cache)
+        probes = np.arange(4, nE, 8)   # 8 energies spread over the band
+        r = hsc.hsc_tune(st_t.h, E[probes], cfg["eta"], sr[probes], sl[probes], cache_path=cache)
         st_t.close()
         sv = hsc.Solver(dev, r["leaf_max"])
         hsc.hsc_set_option(sv.h, hsc.HSC_OPT_GJ_PANEL, r["gj_panel"])
@@ -451,14 +453,13 @@ def run_hsc(args):
     cpu = None
     accuracy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        kq = 20
         t, oref = cpu_oracle_energy(cfg, kq, want_output=True)
         cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "1 energy (E index 20) of the 64-energy grid, RGF sweep, complex128"}
         # the same energy from the timed GPU solve against the oracle's output
         Ls = dev.dims[1] * dev.dims[2]
         u, v = pairs[:, 0] - 15 * Ls, pairs[:, 1] - 16 * Ls
-        got = [t_.cpu().numpy().view(np.complex128)[kq] for t_ in (ogr, ogl, pgr, pgl)]
+        got = timed_out
         refs = [oref["diag_gr"], oref["diag_gl"], oref["coupling_gr"][15][u, v], oref["coupling_gl"][15][u, v]]
         errs = [float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got, refs)]
         accuracy = {"oracle": "RGF sweep (CPU, complex128)", "energy_index": kq,

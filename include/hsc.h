@@ -201,8 +201,9 @@ typedef struct {
 
 /* hsc_tune -- autotune a handle for its geometry on this GPU: for each candidate leaf_max (4, 6, 8,
  *   when smaller than the grid) and Gauss-Jordan panel width (16, 32, 64) re-analyse, solve the given
- *   probe energies twice (host buffers, as hsc_solve, without the residual re-solve: the tuned
- *   settings act on the plain tree) and time the second solve with CUDA events;
+ *   probe energies twice (host buffers, as hsc_solve, residual re-solve included) and time the
+ *   second solve with CUDA events (give it probes spread over the energy window: whether a probe
+ *   needs a re-solve on a given tree weighs in its time);
  *   keep the fastest, leave the handle analysed with it, and append one JSON line (GPU name, grid,
  *   orbitals, precision, choice, time) to cache_path (may be NULL: no cache). A matching cache line
  *   is applied without timing. Errors: as hsc_analyze / hsc_solve. */

@@ -1580,15 +1580,6 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
   double best = 1e300;
   int best_leaf = leaves[0], best_nb = 32, tried = 0;
   (void)ncs;
-  // time the plain tree: which probe energies happen to need a re-solve says nothing about the
-  // leaf size or panel width
-  const int resolve = h->opt_resolve;
-  h->opt_resolve = 0;
-  struct Restore {
-    hsc_ctx* h;
-    int v;
-    ~Restore() { h->opt_resolve = v; }
-  } restore{h, resolve};
   for (int leaf : leaves)
     for (int nb : {16, 32, 64}) {
       int rc = hsc_analyze(h, leaf, nullptr);
