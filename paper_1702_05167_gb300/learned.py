@@ -1,5 +1,5 @@
 """Learned energy grid: an MLP surrogate of log10 T(E) and DOS(E) places an adaptive energy grid;
-the plain selected-inversion solve is both its fallback and the judge of every integrated quantity.
+the plain selected-inversion solve is both its fallback and the arbiter of every integrated quantity.
 
 * Training data: hsc_solve on disorder realisations of a cubic device (W uniform in a range),
   observables (DOS, transmission into the right contact, lesser trace) reduced on the GPU by
@@ -11,7 +11,7 @@ the plain selected-inversion solve is both its fallback and the judge of every i
   densities |T''| h^2 and |DOS''| h^2; points are placed at equal quantiles of
   rho = |T''|^(1/3)/mean + |DOS''|^(1/3)/mean + floor (equidistributing those errors), then the real
   solve runs on them.
-* Judge: integrals (current ~ int T dE, electron count ~ int sum Im G^< dE / 2 pi, int DOS dE) on the
+* Arbiter: integrals (current ~ int T dE, electron count ~ int sum Im G^< dE / 2 pi, int DOS dE) on the
   adaptive grid and on a uniform grid with the same number of points are compared with a dense
   uniform reference computed by the same solver.
 
@@ -165,7 +165,7 @@ def integrals(E, dos, T, ltr):
 
 def evaluate(dev, sur, n_points, n_ref, eta=1e-6, leaf=8, precision=hsc.HSC_FP64):
     """Integrals on the adaptive and on the uniform n_points grids against a uniform n_ref reference,
-    all computed by hsc_solve (the judge)."""
+    all computed by hsc_solve (the arbiter)."""
     feats = disorder_features(dev)
     s = hsc.Solver(dev, leaf)
     res = {}
@@ -189,7 +189,7 @@ def evaluate(dev, sur, n_points, n_ref, eta=1e-6, leaf=8, precision=hsc.HSC_FP64
 def main(argv=None):
     import argparse
     import torch
-    p = argparse.ArgumentParser(description="learned energy grid: train the surrogate, judge the grid")
+    p = argparse.ArgumentParser(description="learned energy grid: train the surrogate, check the grid against plain solves")
     p.add_argument("--train-dims", type=int, default=16)
     p.add_argument("--n-real", type=int, default=64)
     p.add_argument("--n-e", type=int, default=64)
