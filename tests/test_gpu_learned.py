@@ -1,5 +1,5 @@
 """Learned energy grid end to end on a small scale: training data generated by the library's own
-solves, the surrogate trained by its own kernels, the adaptive grid judged by plain solves.
+solves, the surrogate trained by its own kernels, the adaptive grid checked against plain solves.
 
 Reports what the surrogate-placed grid gains over a uniform grid with the same number of points
 (error of each integral against a dense uniform reference); asserts that training converges, that
