@@ -10,7 +10,10 @@ definitions and independent of the CUDA path (no shared code, no shared constant
                   method);
 * ``columns``  -- single columns of G^r by sparse direct solves of A x = e_a, which give G^r_aa and
                   G^<_aa one sampled unknown at a time at any size;
-* ``observables`` -- DOS, transmission (Caroli form) and densities from the oracle's outputs.
+* ``observables`` -- DOS, transmission (Caroli form) and densities from the oracle's outputs;
+* ``scba``     -- the self-consistent loop with local elastic dephasing (the scattering part of
+                  Sigma^r in Eq. 1) around the dense definition, its single-site closed forms and
+                  the terminal currents that its fixed point balances.
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
 package. The product path never does.
