@@ -5,12 +5,17 @@ paper fixes no scattering model. The model written out here is local elastic dep
 self-consistent Born approximation: a delta-correlated scattering potential of strength d0 (eV^2)
 gives, on every unknown u,
 
-    Sigma^r_scatt,uu = d0 G^r_uu,        Sigma^<_scatt,uu = d0 G^<_uu,
+    Sigma^r_scatt,uu = d0 G^r_uu,        Sigma^<_scatt,uu = d0 G^<_uu = i d0 Im G^<_uu,
 
-with G^r and G^< from Eqs. 1-2 evaluated with Sigma = Sigma_contact + Sigma_scatt. The fixed point
+with G^r and G^< from Eqs. 1-2 evaluated with Sigma = Sigma_contact + Sigma_scatt. G^< is
+anti-Hermitian when Sigma^< is (Algorithm 2 relies on it: its downward pass sets the transposed
+block to minus the adjoint), so its diagonal is purely imaginary and the lesser self-energy keeps
+only that part: a real part would be rounding (or conditioning) error with no physical meaning, fed
+back as a Hermitian component that the selected-inversion recurrences do not carry. The fixed point
 is reached by linear mixing, all energies together:
 
-    S_0 = 0;  solve with Sigma_contact + S_k  ->  G_k;  F_k = d0 diag(G_k)  (retarded and lesser);
+    S_0 = 0;  solve with Sigma_contact + S_k  ->  G_k;
+    F_k = (d0 diag G^r_k, i d0 Im diag G^<_k);
     delta_k = max |F_k - S_k| / max |F_k|   (over energies, unknowns, retarded and lesser; 0 if F = 0);
     stop when delta_k <= tol or after max_iter solves, else S_{k+1} = S_k + mix (F_k - S_k).
 
@@ -47,7 +52,7 @@ def scba(H, energies, eta, contact_idx, sigma_r_vals, sigma_less_vals, d0, mix, 
             G = dense.retarded(dense.system_matrix(H, E, eta, sig_r))
             gr[e] = np.diag(G)
             gl[e] = np.diag(dense.lesser(G, sig_l))
-        f_r, f_l = d0 * gr, d0 * gl
+        f_r, f_l = d0 * gr, 1j * d0 * gl.imag
         diff = max(np.abs(f_r - s_r).max(), np.abs(f_l - s_l).max())
         scale = max(np.abs(f_r).max(), np.abs(f_l).max())
         delta = diff / scale if scale > 0 else 0.0
