@@ -95,7 +95,10 @@ int hsc_cluster(hsc_t h, int32_t i, hsc_cluster_info* info, int32_t* own, int32_
 /* hsc_solve -- selected G^r and G^< at n_E energies (Algorithms 1 and 2).
  *   E[n_E]                energies (eV); eta (eV) > 0 recommended (eta = 0 may be singular)
  *   sigma_r[n_E][n_cs]    diagonal Sigma^r on the n_cs contact slots, per energy
- *   sigma_less[n_E][n_cs] diagonal Sigma^< per energy, or NULL: G^< work and outputs are skipped
+ *   sigma_less[n_E][n_cs] diagonal Sigma^< per energy, or NULL: G^< work and outputs are skipped.
+ *                         Sigma^< must be anti-Hermitian (purely imaginary diagonal, i f Gamma for a
+ *                         contact): Algorithm 2 builds G^< from that symmetry, and a real part is
+ *                         not carried consistently
  *   precision             HSC_FP64: complex128 storage, every block product on the FP64 pipe.
  *                         HSC_MIXED: complex128 storage; block products below the top tree levels
  *                         (HSC_FP64_LEVELS, default 2: the root and its children stay FP64) run on
@@ -263,6 +266,33 @@ int hsc_profile_read(hsc_t h, hsc_kernel_stat* out, int32_t cap, int32_t* n_out)
  *   Errors: HSC_ERR_ARG, HSC_ERR_STATE, HSC_ERR_CUDA. */
 int hsc_observables(hsc_t h, int64_t n_E, const hsc_c128* diag_gr, const hsc_c128* diag_gl,
                     const hsc_c128* sigma_r, int32_t contact, double* out, void* cuda_stream);
+
+/* hsc_scba -- self-consistent loop with the solve as its inner kernel: local elastic dephasing as
+ *   the scattering part of Sigma^r (Section 1 splits Sigma^r of Eq. 1 into a contact part and a
+ *   scattering part; the paper fixes no scattering model, this is the local one of the
+ *   self-consistent Born approximation with a delta-correlated potential of strength d0, eV^2):
+ *     Sigma^r_scatt,uu = d0 G^r_uu,  Sigma^<_scatt,uu = d0 G^<_uu = i d0 Im G^<_uu  on every
+ *   unknown u (G^< is anti-Hermitian, so the real part of its diagonal is rounding error and is
+ *   not fed back: see the Sigma^< convention of hsc_solve).
+ *   Iteration, all energies together: S_0 = 0; hsc_solve with Sigma_contact + S_k gives G_k;
+ *   F_k = (d0 diag G^r_k, i d0 Im diag G^<_k); delta_k = max|F_k - S_k| / max|F_k| over energies,
+ *   unknowns, retarded and lesser (0 when F_k = 0); stop when delta_k <= tol or after max_iter
+ *   solves; else S_{k+1} = S_k + mix (F_k - S_k). The mixing and both maxima run in one kernel; the
+ *   host reads two doubles per iteration.
+ *   The handle's contacts must cover every site: declare the scattering region (for instance every
+ *   site outside the leads) as one more contact whose contact self-energy is zero.
+ *   E, sigma_r, sigma_less, precision, cuda_stream, io_on_device: as hsc_solve; sigma_r and
+ *     sigma_less[n_E][n_cs] are the contact parts (sigma_less is required)
+ *   d0 >= 0, 0 < mix <= 1, tol >= 0, max_iter >= 1
+ *   diag_gr, diag_gl[n_E][n]  out: the diagonals of the last solve (the one delta_k was measured on)
+ *   iters, delta  out (host): solves made and the last delta_k. Reaching max_iter is not an error:
+ *     compare *delta with tol.
+ *   Device work memory for the self-energies (4 n_E n_cs complex) is allocated per call.
+ *   Errors: as hsc_solve; HSC_ERR_ARG also when the contacts leave a site out. */
+int hsc_scba(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+             const hsc_c128* sigma_less, double d0, double mix, double tol, int32_t max_iter,
+             int32_t precision, hsc_c128* diag_gr, hsc_c128* diag_gl, int32_t* iters, double* delta,
+             void* cuda_stream, int32_t io_on_device);
 
 /* hsc_device_fp64_peaks -- measure, on the current device, the throughput of the FP64 tensor pipe
  *   (mma.sync m8n8k4 f64, which the complex128 GEMMs use) and of scalar FP64 FMA, in GFLOP/s

@@ -523,7 +523,58 @@ __global__ void k_observables(int64_t n, const c64* gr, const c64* gl, const c64
   }
 }
 
+// ---- self-consistent dephasing (the scattering part of Sigma^r in Eq. 1, local elastic model):
+//      on every contact slot k of energy e, with u its unknown, F^r = d0 G^r_uu and F^< = i d0 Im G^<_uu
+//      (G^< is anti-Hermitian, Algorithm 2: a real part of its diagonal is rounding error, and fed
+//      back it would be a Hermitian part of Sigma^< that the lesser recurrences do not carry);
+//      delta = max |F - S| and scale = max |F| over all slots (atomicMax on the bit patterns of
+//      non-negative doubles, whose unsigned order is their numeric order); then S += mix (F - S)
+//      and the next solve's self-energy Sigma = Sigma_contact + S.
+__global__ void k_scba_mix(int64_t total, int64_t n, int64_t ncs, const int64_t* slot_unknown,
+                           const c64* gr, const c64* gl, const c64* cr, const c64* cl, double d0,
+                           double mix, c64* s_r, c64* s_l, c64* sig_r, c64* sig_l,
+                           unsigned long long* dmax) {
+  double dm = 0.0, sc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / ncs;
+    const int64_t u = e * n + slot_unknown[i - e * ncs];
+    const c64 fr = make_double2(d0 * gr[u].x, d0 * gr[u].y);
+    const c64 fl = make_double2(0.0, d0 * gl[u].y);
+    c64 a = s_r[i], b = s_l[i];
+    const c64 dr = csub(fr, a), dl = csub(fl, b);
+    dm = fmax(dm, fmax(hypot(dr.x, dr.y), hypot(dl.x, dl.y)));
+    sc = fmax(sc, fmax(hypot(fr.x, fr.y), hypot(fl.x, fl.y)));
+    a = make_double2(a.x + mix * dr.x, a.y + mix * dr.y);
+    b = make_double2(b.x + mix * dl.x, b.y + mix * dl.y);
+    s_r[i] = a;
+    s_l[i] = b;
+    sig_r[i] = cadd(cr[i], a);
+    sig_l[i] = cadd(cl[i], b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(dm));
+    atomicMax(&dmax[1], (unsigned long long)__double_as_longlong(sc));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_scba_mix(int64_t n_E, int64_t n, int64_t ncs, const int64_t* slot_unknown,
+                            const c64* gr, const c64* gl, const c64* cr, const c64* cl, double d0,
+                            double mix, c64* s_r, c64* s_l, c64* sig_r, c64* sig_l,
+                            unsigned long long* dmax, cudaStream_t s) {
+  const int64_t total = n_E * ncs;
+  if (total <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
+  k_scba_mix<<<(unsigned)blocks, 256, 0, s>>>(total, n, ncs, slot_unknown, gr, gl, cr, cl, d0, mix, s_r,
+                                               s_l, sig_r, sig_l, dmax);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_observables(int64_t n_E, int64_t n, const c64* gr, const c64* gl, const c64* sr,
                                int64_t ncs, const int64_t* slot_unknown, const int32_t* slot_contact,

@@ -931,8 +931,6 @@ int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
   }
   if (n_req > d->pair_cap) {
     if (d->poff) cudaFree(d->poff);
-  if (d->slot_unknown) cudaFree(d->slot_unknown);
-  if (d->slot_contact) cudaFree(d->slot_contact);
     d->poff = nullptr;
     d->pair_cap = 0;
     if (cudaMalloc((void**)&d->poff, (size_t)n_req * sizeof(int64_t)) != cudaSuccess) {
@@ -942,6 +940,34 @@ int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
     d->pair_cap = n_req;
   }
   if (n_req > 0) CK(cudaMemcpy(d->poff, poff.data(), n_req * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return HSC_OK;
+}
+
+// Uploads, once per device state, the unknown and the contact id of every contact slot.
+int ensure_slots(hsc_ctx* h) {
+  DeviceState* d = h->dev;
+  if (d->slot_unknown || h->n_contact_unknowns == 0) return HSC_OK;
+  std::vector<int64_t> su;
+  std::vector<int32_t> sc;
+  for (int c = 0; c < h->n_contacts; ++c)
+    for (int64_t k = h->contact_ptr[c]; k < h->contact_ptr[c + 1]; ++k)
+      for (int o = 0; o < h->orb; ++o) {
+        su.push_back((int64_t)h->contact_sites[k] * h->orb + o);
+        sc.push_back(c);
+      }
+  cudaError_t e = upload(d, &d->slot_unknown, su);
+  if (e == cudaSuccess) e = upload(d, &d->slot_contact, sc);
+  // upload() also lists them in `fixed`; device_state_free frees them by name
+  while (!d->fixed.empty() && (d->fixed.back() == d->slot_unknown || d->fixed.back() == d->slot_contact))
+    d->fixed.pop_back();
+  if (e != cudaSuccess) {
+    if (d->slot_unknown) cudaFree(d->slot_unknown);
+    if (d->slot_contact) cudaFree(d->slot_contact);
+    d->slot_unknown = nullptr;
+    d->slot_contact = nullptr;
+    cudaGetLastError();
+    return hsc_fail(h, HSC_ERR_CUDA, "upload contact slots");
+  }
   return HSC_OK;
 }
 
@@ -1633,28 +1659,105 @@ extern "C" int hsc_observables(hsc_t h, int64_t n_E, const hsc_c128* diag_gr, co
   if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
   int rc = get_state(h);
   if (rc != HSC_OK) return rc;
+  if ((rc = hsc::ensure_slots(h)) != HSC_OK) return rc;
   DeviceState* d = h->dev;
   const int64_t ncs = h->n_contact_unknowns;
-  if (!d->slot_unknown && ncs > 0) {
-    std::vector<int64_t> su;
-    std::vector<int32_t> sc;
-    for (int c = 0; c < h->n_contacts; ++c)
-      for (int64_t k = h->contact_ptr[c]; k < h->contact_ptr[c + 1]; ++k)
-        for (int o = 0; o < h->orb; ++o) {
-          su.push_back((int64_t)h->contact_sites[k] * h->orb + o);
-          sc.push_back(c);
-        }
-    cudaError_t e = upload(d, &d->slot_unknown, su);
-    if (e == cudaSuccess) e = upload(d, &d->slot_contact, sc);
-    if (e != cudaSuccess) return hsc_fail(h, HSC_ERR_CUDA, "upload contact slots");
-    // owned by `fixed` through upload(); do not free twice
-    d->fixed.pop_back();
-    d->fixed.pop_back();
-  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(launch_observables(n_E, h->n, reinterpret_cast<const c64*>(diag_gr),
                         reinterpret_cast<const c64*>(diag_gl), reinterpret_cast<const c64*>(sigma_r), ncs,
                         d->slot_unknown, d->slot_contact, contact, out, s));
+  return HSC_OK;
+}
+
+extern "C" int hsc_scba(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                        const hsc_c128* sigma_less, double d0, double mix, double tol, int32_t max_iter,
+                        int32_t precision, hsc_c128* diag_gr, hsc_c128* diag_gl, int32_t* iters,
+                        double* delta, void* cuda_stream, int32_t io_on_device) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!iters || !delta || n_E < 0 ||
+      (n_E > 0 && (!E || !sigma_r || !sigma_less || !diag_gr || !diag_gl)))
+    return hsc_fail(h, HSC_ERR_ARG, "bad SCBA arguments");
+  if (!(d0 >= 0.0) || !(mix > 0.0 && mix <= 1.0) || !(tol >= 0.0) || max_iter < 1)
+    return hsc_fail(h, HSC_ERR_ARG, "need d0 >= 0, 0 < mix <= 1, tol >= 0 and max_iter >= 1");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  if (h->n_contact_unknowns != h->n)
+    return hsc_fail(h, HSC_ERR_ARG,
+                    "dephasing acts on every unknown: the contacts must cover every site (declare the "
+                    "scattering region as a contact whose contact self-energy is zero)");
+  *iters = 0;
+  *delta = 0.0;
+  if (n_E == 0) return HSC_OK;
+  int rc = get_state(h);
+  if (rc != HSC_OK) return rc;
+  if ((rc = hsc::ensure_slots(h)) != HSC_OK) return rc;
+  const int64_t n = h->n, ncs = h->n_contact_unknowns, slots = n_E * ncs;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // device work: S_r, S_l, Sigma_r, Sigma_l per slot, the two maxima; with host I/O also E, the
+  // contact parts and the diagonals
+  struct Work {
+    void* p = nullptr;
+    ~Work() { if (p) cudaFree(p); }
+  } work;
+  auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+  int64_t bytes = 4 * up(slots * 16) + 256;
+  if (!io_on_device) bytes += up(n_E * 8) + 2 * up(slots * 16) + 2 * up(n_E * n * 16);
+  if (cudaMalloc(&work.p, bytes) != cudaSuccess) {
+    work.p = nullptr;
+    cudaGetLastError();
+    return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc SCBA work");
+  }
+  char* q = (char*)work.p;
+  auto take = [&](int64_t b) { char* r = q; q += up(b); return r; };
+  c64* s_r = (c64*)take(slots * 16);
+  c64* s_l = (c64*)take(slots * 16);
+  c64* sig_r = (c64*)take(slots * 16);
+  c64* sig_l = (c64*)take(slots * 16);
+  unsigned long long* dmax = (unsigned long long*)take(256);
+  const double* dE = E;
+  const c64* cr = reinterpret_cast<const c64*>(sigma_r);
+  const c64* cl = reinterpret_cast<const c64*>(sigma_less);
+  c64* gr = reinterpret_cast<c64*>(diag_gr);
+  c64* gl = reinterpret_cast<c64*>(diag_gl);
+  if (!io_on_device) {
+    double* hE = (double*)take(n_E * 8);
+    c64* hcr = (c64*)take(slots * 16);
+    c64* hcl = (c64*)take(slots * 16);
+    gr = (c64*)take(n_E * n * 16);
+    gl = (c64*)take(n_E * n * 16);
+    CK(cudaMemcpyAsync(hE, E, n_E * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(hcr, sigma_r, slots * 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(hcl, sigma_less, slots * 16, cudaMemcpyHostToDevice, s));
+    dE = hE;
+    cr = hcr;
+    cl = hcl;
+  }
+  CK(cudaMemsetAsync(s_r, 0, 2 * up(slots * 16), s));   // S_r and S_l: S_0 = 0
+  CK(cudaMemcpyAsync(sig_r, cr, slots * 16, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sig_l, cl, slots * 16, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < max_iter; ++k) {
+    rc = hsc_solve(h, n_E, dE, eta, reinterpret_cast<const hsc_c128*>(sig_r),
+                   reinterpret_cast<const hsc_c128*>(sig_l), precision, 0, nullptr,
+                   reinterpret_cast<hsc_c128*>(gr), reinterpret_cast<hsc_c128*>(gl), nullptr, nullptr, s, 1);
+    if (rc != HSC_OK) return rc;
+    CK(cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned long long), s));
+    CK(launch_scba_mix(n_E, n, ncs, h->dev->slot_unknown, gr, gl, cr, cl, d0, mix, s_r, s_l, sig_r, sig_l,
+                       dmax, s));
+    unsigned long long m[2] = {0, 0};
+    CK(cudaMemcpyAsync(m, dmax, sizeof(m), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double diff, scale;
+    std::memcpy(&diff, &m[0], 8);
+    std::memcpy(&scale, &m[1], 8);
+    *iters = k + 1;
+    *delta = scale > 0.0 ? diff / scale : 0.0;
+    if (*delta <= tol) break;
+  }
+  if (!io_on_device) {
+    CK(cudaMemcpyAsync(diag_gr, gr, n_E * n * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(diag_gl, gl, n_E * n * 16, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  h->err.clear();
   return HSC_OK;
 }
 

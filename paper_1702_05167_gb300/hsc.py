@@ -20,7 +20,7 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
            "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read", "hsc_growth",
            "hsc_residual",
-           "hsc_device_fp64_peaks", "hsc_observables", "hsc_last_error", "hsc_destroy",
+           "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba", "hsc_last_error", "hsc_destroy",
            "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
            "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF, HSC_OPT_COMPLEX_4M = 1, 2, 3, 4, 5
@@ -94,6 +94,8 @@ def load():
     L.hsc_set_option.argtypes = [vp, i32, i32]
     L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
     L.hsc_observables.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp]
+    L.hsc_scba.argtypes = [vp, i64, vp, dp, vp, vp, dp, dp, dp, i32, i32, vp, vp,
+                           ctypes.POINTER(i32), ctypes.POINTER(dp), vp, i32]
     L.hsc_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32]
     L.hsc_mlp_num_params.argtypes = [vp, ctypes.POINTER(i64)]
     L.hsc_mlp_set_params.argtypes = [vp, vp]
@@ -188,6 +190,20 @@ def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, dia
                             int(precision), n_req, _ptr(pairs), _ptr(diag_gr), _ptr(diag_gl),
                             _ptr(req_gr), _ptr(req_gl), s, 1 if io_on_device else 0)
     _check(h, code)
+
+
+def hsc_scba(h, E, eta, sigma_r, sigma_less, d0, mix, tol, max_iter, precision, diag_gr, diag_gl,
+             stream=None, io_on_device=False):
+    """Marshal buffers to hsc_scba (as hsc_solve). Returns (solves made, last delta)."""
+    it = ctypes.c_int32()
+    dl = ctypes.c_double()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    code = load().hsc_scba(h, int(E.shape[0]), _ptr(E), float(eta), _ptr(sigma_r), _ptr(sigma_less),
+                           float(d0), float(mix), float(tol), int(max_iter), int(precision),
+                           _ptr(diag_gr), _ptr(diag_gl), ctypes.byref(it), ctypes.byref(dl), s,
+                           1 if io_on_device else 0)
+    _check(h, code)
+    return it.value, dl.value
 
 
 def hsc_set_option(h, option, value):

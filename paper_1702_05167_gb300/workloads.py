@@ -170,6 +170,18 @@ def chain_device(N, t=-1.0, eps=None, gamma=0.5):
                   gamma=np.array([gamma, gamma]), meta=dict(kind="chain", t=t, onsite=eps))
 
 
+def with_scattering_contact(dev: Device) -> Device:
+    """Copy of dev with one more contact holding every site outside its contacts, broadening 0: the
+    scattering region, so that every unknown has a self-energy slot."""
+    inside = np.zeros(dev.n_sites, dtype=bool)
+    inside[dev.contact_sites] = True
+    rest = np.nonzero(~inside)[0].astype(np.int32)
+    ptr = np.append(dev.contact_ptr, dev.contact_ptr[-1] + len(rest)).astype(np.int64)
+    return Device(dims=dev.dims, orb=dev.orb, rowptr=dev.rowptr, col=dev.col, val=dev.val,
+                  contact_ptr=ptr, contact_sites=np.concatenate([dev.contact_sites, rest]),
+                  gamma=np.append(dev.gamma, 0.0), meta=dict(dev.meta, scattering_contact=True))
+
+
 def self_energies(dev: Device, n_E: int, f=(1.0, 0.0)):
     """Diagonal wide-band self-energies over dev.contact_unknowns() for n_E energies.
 

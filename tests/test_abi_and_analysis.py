@@ -165,6 +165,29 @@ def test_degenerate_chain_tree():
     assert st.max_n == 1 and st.max_m <= 2
 
 
+def test_scba_rejects_uncovered_sites_and_bad_parameters():
+    """hsc_scba needs a self-energy slot on every unknown and sane loop parameters; both are
+    checked on the host before any device work."""
+    E = np.array([0.1])
+    for dev, ok in ((W.cubic_device((4, 4, 4), seed=0), False),
+                    (W.with_scattering_contact(W.cubic_device((4, 4, 4), seed=0)), True)):
+        h = _handle(dev)
+        hsc.hsc_analyze(h, 2)
+        ncs = len(dev.contact_unknowns())
+        sr = np.zeros((1, ncs), np.complex128)
+        out = np.zeros((1, dev.n), np.complex128)
+        for d0, mix, tol, it in ((-0.1, 0.5, 1e-8, 10), (0.1, 0.0, 1e-8, 10), (0.1, 1.5, 1e-8, 10),
+                                 (0.1, 0.5, -1.0, 10), (0.1, 0.5, 1e-8, 0)):
+            with pytest.raises(hsc.HSCError) as ei:
+                hsc.hsc_scba(h, E, 1e-6, sr, sr.copy(), d0, mix, tol, it, hsc.HSC_FP64, out, out.copy())
+            assert ei.value.code == hsc.HSC_ERR_ARG
+        if not ok:
+            with pytest.raises(hsc.HSCError) as ei:
+                hsc.hsc_scba(h, E, 1e-6, sr, sr.copy(), 0.1, 0.5, 1e-8, 10, hsc.HSC_FP64, out, out.copy())
+            assert ei.value.code == hsc.HSC_ERR_ARG and "cover every site" in str(ei.value)
+        hsc.hsc_destroy(h)
+
+
 def test_options_round_trip_and_reject_bad_values():
     dev = W.cubic_device((4, 4, 4), seed=0)
     h = _handle(dev)
