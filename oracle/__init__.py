@@ -11,6 +11,8 @@ definitions and independent of the CUDA path (no shared code, no shared constant
 * ``columns``  -- single columns of G^r by sparse direct solves of A x = e_a, which give G^r_aa and
                   G^<_aa one sampled unknown at a time at any size;
 * ``observables`` -- DOS, transmission (Caroli form) and densities from the oracle's outputs;
+* ``lead``     -- open-boundary (DENSE) contact self-energies of Section 3.1.2: the surface Green's
+                  function of a semi-infinite lead by decimation, Sigma^r = tau g_s tau^T, Gamma;
 * ``scba``     -- the self-consistent loop with local elastic dephasing (the scattering part of
                   Sigma^r in Eq. 1) around the dense definition, its single-site closed forms and
                   the terminal currents that its fixed point balances.

@@ -182,6 +182,23 @@ def with_scattering_contact(dev: Device) -> Device:
                   gamma=np.append(dev.gamma, 0.0), meta=dict(dev.meta, scattering_contact=True))
 
 
+def cubic_lead(dims, t=-1.0):
+    """Clean semi-infinite lead continuing a cubic device along x: the layer Hamiltonian H00 (the
+    Ny x Nz cross-section, onsite 0, hopping t) and the coupling H01 from one layer to the next
+    (t on every site). Face-local site order y * Nz + z, as face_sites."""
+    _, Ny, Nz = (int(d) for d in dims)
+    m = Ny * Nz
+    H00 = np.zeros((m, m), dtype=np.complex128)
+    for y in range(Ny):
+        for z in range(Nz):
+            a = y * Nz + z
+            if y + 1 < Ny:
+                H00[a, a + Nz] = H00[a + Nz, a] = t
+            if z + 1 < Nz:
+                H00[a, a + 1] = H00[a + 1, a] = t
+    return H00, t * np.eye(m, dtype=np.complex128)
+
+
 def self_energies(dev: Device, n_E: int, f=(1.0, 0.0)):
     """Diagonal wide-band self-energies over dev.contact_unknowns() for n_E energies.
 
