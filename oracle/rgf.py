@@ -46,11 +46,14 @@ def layer_blocks(H, layer_size):
     return Hd, Hu, Hl
 
 
-def sweep(H, layer_size, E, eta, contact_idx, sigma_r_vals, sigma_less_vals, coupling_layers=()):
+def sweep(H, layer_size, E, eta, contact_idx, sigma_r_vals, sigma_less_vals, coupling_layers=(),
+          dense_r=None, dense_l=None):
     """Selected G^r and G^< at one energy by RGF (Section 2.1, Eqs. 3-4 and Eq. 2).
 
     H: scipy sparse n x n; contact_idx/sigma_*_vals: diagonal self-energies (they must lie in the
     first and last layers); coupling_layers: layer indices n for which G_{n,n+1} blocks are returned.
+    dense_r, dense_l: optional (first-layer block, last-layer block) of a DENSE Sigma^r / Sigma^<
+    (Section 3.1.2), layer-local numbering, added to the diagonal ones; they need two layers or more.
     Returns dict(diag_gr, diag_gl, coupling_gr={n: block}, coupling_gl={n: block}).
     """
     n = H.shape[0]
@@ -70,6 +73,11 @@ def sweep(H, layer_size, E, eta, contact_idx, sigma_r_vals, sigma_less_vals, cou
     z = E + 1j * eta
     # A blocks (Eq. 1): A_nn = z I - H_nn - Sigma^r_n, A_{n,n+1} = -H_{n,n+1}, A_{n+1,n} = -H_{n+1,n}
     Ad = [z * eye - Hd[k] - np.diag(sr[k * Ls:(k + 1) * Ls]) for k in range(N)]
+    if (dense_r is not None or dense_l is not None) and N < 2:
+        raise ValueError("dense contact blocks need at least two layers")
+    if dense_r is not None:
+        Ad[0] = Ad[0] - dense_r[0]
+        Ad[N - 1] = Ad[N - 1] - dense_r[1]
     Au = [-h for h in Hu]
     Al = [-h for h in Hl]
 
@@ -110,11 +118,21 @@ def sweep(H, layer_size, E, eta, contact_idx, sigma_r_vals, sigma_less_vals, cou
     for k in range(1, N):
         col1[k] = -gR[k] @ Al[k - 1] @ col1[k - 1]
     diag_gl = np.empty(n, dtype=np.complex128)
-    for k in range(N):
-        a, b = col1[k], colN[k]
-        diag_gl[k * Ls:(k + 1) * Ls] = ((np.abs(a) ** 2) @ s1) + ((np.abs(b) ** 2) @ sN) \
-            if N > 1 else (np.abs(a) ** 2) @ s1
     coupling_gl = {}
-    for k in coupling_layers:
-        coupling_gl[k] = (col1[k] * s1) @ col1[k + 1].conj().T + (colN[k] * sN) @ colN[k + 1].conj().T
+    if dense_l is None:
+        for k in range(N):
+            a, b = col1[k], colN[k]
+            diag_gl[k * Ls:(k + 1) * Ls] = ((np.abs(a) ** 2) @ s1) + ((np.abs(b) ** 2) @ sN) \
+                if N > 1 else (np.abs(a) ** 2) @ s1
+        for k in coupling_layers:
+            coupling_gl[k] = (col1[k] * s1) @ col1[k + 1].conj().T + (colN[k] * sN) @ colN[k + 1].conj().T
+    else:   # Sigma^<_1, Sigma^<_N full blocks: G^<_ab = G_a1 S_1 G_b1^dagger + G_aN S_N G_bN^dagger
+        S1 = np.diag(s1) + dense_l[0]
+        SN = np.diag(sN) + dense_l[1]
+        for k in range(N):
+            a, b = col1[k], colN[k]
+            diag_gl[k * Ls:(k + 1) * Ls] = np.einsum("ij,jk,ik->i", a, S1, a.conj()) + \
+                np.einsum("ij,jk,ik->i", b, SN, b.conj())
+        for k in coupling_layers:
+            coupling_gl[k] = col1[k] @ S1 @ col1[k + 1].conj().T + colN[k] @ SN @ colN[k + 1].conj().T
     return dict(diag_gr=diag_gr, diag_gl=diag_gl, coupling_gr=coupling_gr, coupling_gl=coupling_gl)

@@ -88,3 +88,31 @@ def test_perfect_wire_transmits_one_per_open_channel(E):
     em = (2 * t * np.cos(np.pi * k / (dims[1] + 1)))[:, None] + (2 * t * np.cos(np.pi * l / (dims[2] + 1)))[None, :]
     open_channels = int((np.abs(E - em) < 2 * abs(t)).sum())
     assert abs(T - open_channels) <= 1e-6
+
+
+@pytest.mark.parametrize("E", [-2.7, -0.9, 0.4, 1.8])
+def test_rgf_with_dense_contacts_matches_the_dense_definition(E):
+    """The RGF sweep with DENSE first/last-layer self-energies (lead surface Green's functions)
+    against Eqs. 1-2 written out with the same blocks embedded: diag G^r, diag G^< and the
+    coupling blocks of two layer pairs."""
+    from oracle import rgf
+    dims, t, eta = (5, 3, 4), -1.0, 1e-6
+    dev = W.cubic_device(dims, t=t, W=1.0, seed=6)
+    Hs = dev.to_scipy()
+    H00, H01 = W.cubic_lead(dims, t=t)
+    tau = t * np.eye(H00.shape[0])
+    S = lead.contact_self_energy(E, eta, H00, H01, tau)
+    Sl = 1j * lead.broadening(S)          # left lead filled (f = 1), right lead empty
+    Z = np.zeros_like(S)
+    Ls = dims[1] * dims[2]
+    out = rgf.sweep(Hs, Ls, E, eta, [], [], [], coupling_layers=(1, 3), dense_r=(S, S), dense_l=(Sl, Z))
+    left, right = W.face_sites(dims, 0), W.face_sites(dims, dims[0] - 1)
+    A = dense.system_matrix(Hs.toarray(), E, eta, lead.embed_blocks(dev.n, [(left, S), (right, S)]))
+    G = dense.retarded(A)
+    Gl = dense.lesser(G, lead.embed_blocks(dev.n, [(left, Sl)]))
+    assert np.abs(out["diag_gr"] - np.diag(G)).max() <= 1e-11 * np.abs(np.diag(G)).max()
+    assert np.abs(out["diag_gl"] - np.diag(Gl)).max() <= 1e-11 * np.abs(np.diag(Gl)).max()
+    for k in (1, 3):
+        a, b = slice(k * Ls, (k + 1) * Ls), slice((k + 1) * Ls, (k + 2) * Ls)
+        assert np.abs(out["coupling_gr"][k] - G[a, b]).max() <= 1e-11 * np.abs(G[a, b]).max()
+        assert np.abs(out["coupling_gl"][k] - Gl[a, b]).max() <= 1e-11 * np.abs(Gl[a, b]).max()
