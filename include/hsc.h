@@ -86,6 +86,18 @@ int hsc_create(hsc_t* out, int64_t n, int32_t orb,
  *   at leaf_max^3 sites. stats may be NULL. Errors: HSC_ERR_ARG, HSC_ERR_OOM. */
 int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats);
 
+/* hsc_set_contact_dense -- mark contact `contact` as DENSE (dense = 1) or diagonal (0, the default).
+ *   Section 3.1.2 models open boundaries with a dense self-energy block on the contact layer, which
+ *   couples every pair of the contact's unknowns. The next hsc_analyze then keeps each dense
+ *   contact's unknowns in one cluster, chained on top of the nested dissection of the remaining
+ *   sites (geometric dissection of the interior box when the dense contacts are whole end planes
+ *   x = 0 / x = Nx-1, else graph bisection of the rest), so that block stays inside one front.
+ *   The call discards the handle's tree and device state: hsc_analyze must run again.
+ *   Solves on such a tree take the diagonal self-energies of hsc_solve; the dense block itself is
+ *   not an input of hsc_solve yet.
+ *   Errors: HSC_ERR_ARG (contact out of range, dense not 0 or 1). */
+int hsc_set_contact_dense(hsc_t h, int32_t contact, int32_t dense);
+
 /* hsc_cluster -- describe cluster i (postorder id, root = n_clusters-1) after hsc_analyze.
  *   own/upd: optional host arrays of at least n / m int32 entries receiving the user-order unknowns
  *   of the cluster and of its update set U_i (ascending in the cluster ordering).

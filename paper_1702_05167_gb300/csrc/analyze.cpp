@@ -163,16 +163,61 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
     a.erase(std::unique(a.begin(), a.end()), a.end());
   }
 
+  // DENSE contacts (Section 3.1.2): a dense self-energy block couples every pair of the contact's
+  // unknowns, so each such contact becomes one cluster, chained on top of the nested dissection of
+  // the remaining sites (an ancestor of every other cluster, so the update sets stay exact).
+  std::vector<int> dense_c;
+  std::vector<char> in_dense(ns, 0);
+  int64_t n_dense = 0;
+  for (int c = 0; c < in.n_contacts; ++c) {
+    if (!in.contact_dense || !in.contact_dense[c]) continue;
+    dense_c.push_back(c);
+    for (int64_t k = in.contact_ptr[c]; k < in.contact_ptr[c + 1]; ++k) {
+      const int s = in.contact_sites[k];
+      if (s < 0 || s >= ns) return "contact site out of range";
+      if (in_dense[s]) return "site appears in two contacts";
+      in_dense[s] = 1;
+      ++n_dense;
+    }
+  }
   bool geo = in.dims[0] > 0 && in.dims[1] > 0 && in.dims[2] > 0;
+  if (geo && (int64_t)in.dims[0] * in.dims[1] * in.dims[2] != ns) return "grid_dims do not match n/orb";
+  int x0 = 0, x1 = geo ? in.dims[0] - 1 : 0;
+  if (geo && n_dense > 0) {
+    // geometric dissection of the interior box when the dense contacts are whole end planes x = 0
+    // and x = Nx-1; any other dense contact shape falls back to graph bisection of the rest
+    const int64_t plane = (int64_t)in.dims[1] * in.dims[2];
+    int64_t faces = 0;
+    for (int c : dense_c) {
+      const int64_t cnt = in.contact_ptr[c + 1] - in.contact_ptr[c];
+      const int s0 = in.contact_sites[in.contact_ptr[c]];
+      const int x = (int)(s0 / plane);
+      bool face = cnt == plane && (x == 0 || x == in.dims[0] - 1) && !(x == 0 && x0 > 0) &&
+                  !(x == in.dims[0] - 1 && x1 < in.dims[0] - 1);
+      for (int64_t k = in.contact_ptr[c]; face && k < in.contact_ptr[c + 1]; ++k)
+        face = in.contact_sites[k] / plane == x;
+      if (!face) { geo = false; break; }
+      if (x == 0) x0 = 1;
+      else x1 = in.dims[0] - 2;
+      faces += cnt;
+    }
+    if (geo && faces != n_dense) geo = false;
+  }
+  int top = -1;
   if (geo) {
-    if ((int64_t)in.dims[0] * in.dims[1] * in.dims[2] != ns) return "grid_dims do not match n/orb";
-    int lo[3] = {0, 0, 0}, hi[3] = {in.dims[0] - 1, in.dims[1] - 1, in.dims[2] - 1};
-    B.box(lo, hi);
+    int lo[3] = {x0, 0, 0}, hi[3] = {x1, in.dims[1] - 1, in.dims[2] - 1};
+    top = x0 <= x1 ? B.box(lo, hi) : -1;
   } else {
-    std::vector<int> all(ns);
-    std::iota(all.begin(), all.end(), 0);
+    std::vector<int> rest;
+    rest.reserve(ns - n_dense);
+    for (int64_t s = 0; s < ns; ++s)
+      if (!in_dense[s]) rest.push_back((int)s);
     std::vector<int> mark(ns, -1);
-    B.graph(std::move(all), mark, 0);
+    top = B.graph(std::move(rest), mark, 0);
+  }
+  for (int c : dense_c) {
+    std::vector<int> sites(in.contact_sites + in.contact_ptr[c], in.contact_sites + in.contact_ptr[c + 1]);
+    top = B.make(std::move(sites), top, -1);
   }
   auto& cl = P.cl;
   const int nc = (int)cl.size();

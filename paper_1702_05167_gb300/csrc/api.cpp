@@ -116,6 +116,7 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   in.contact_sites = h->contact_sites.data();
   std::memcpy(in.dims, h->dims, sizeof(in.dims));
   in.variant = h->nd_variant;
+  in.contact_dense = h->contact_dense.empty() ? nullptr : h->contact_dense.data();
   hsc_drop_alt(h);   // the twin follows the leaf size of this analysis
   std::string e;
   try {
@@ -227,6 +228,21 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
   return HSC_OK;
 }
 
+extern "C" int hsc_set_contact_dense(hsc_t h, int32_t contact, int32_t dense) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (h->is_alt || contact < 0 || contact >= h->n_contacts || (dense != 0 && dense != 1))
+    return hsc_fail(h, HSC_ERR_ARG, "contact out of range or dense not 0/1");
+  h->contact_dense.resize(h->n_contacts, 0);
+  h->contact_dense[contact] = (char)dense;
+  // the cluster tree depends on it: the handle must be analysed again
+  h->analyzed = false;
+  hsc::device_state_free(h->dev);
+  h->dev = nullptr;
+  hsc_drop_alt(h);
+  h->err.clear();
+  return HSC_OK;
+}
+
 extern "C" const char* hsc_last_error(hsc_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 void hsc_drop_alt(hsc_ctx* h) {
@@ -253,6 +269,7 @@ hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
   a->contact_ptr = h->contact_ptr;
   a->contact_sites = h->contact_sites;
   a->n_contact_unknowns = h->n_contact_unknowns;
+  a->contact_dense = h->contact_dense;
   std::memcpy(a->dims, h->dims, sizeof(a->dims));
   a->opt_nb = h->opt_nb;
   a->opt_fp64_levels = h->opt_fp64_levels;

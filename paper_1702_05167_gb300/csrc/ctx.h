@@ -21,6 +21,7 @@ struct hsc_ctx {
   std::vector<int64_t> contact_ptr;
   std::vector<int32_t> contact_sites;
   int64_t n_contact_unknowns = 0;
+  std::vector<char> contact_dense;   // per contact: 1 = DENSE self-energy block (hsc_set_contact_dense)
   int dims[3] = {0, 0, 0};
   bool analyzed = false;
   hsc::Plan plan;

@@ -18,7 +18,8 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
           8: "HSC_ERR_TIMEOUT"}
 
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
-           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile", "hsc_profile_read", "hsc_growth",
+           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_set_contact_dense", "hsc_profile",
+           "hsc_profile_read", "hsc_growth",
            "hsc_residual",
            "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba", "hsc_last_error", "hsc_destroy",
            "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
@@ -92,6 +93,7 @@ def load():
     L.hsc_tune.argtypes = [vp, i64, vp, dp, vp, vp, i32, ctypes.c_char_p,
                            ctypes.POINTER(hsc_tune_result)]
     L.hsc_set_option.argtypes = [vp, i32, i32]
+    L.hsc_set_contact_dense.argtypes = [vp, i32, i32]
     L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
     L.hsc_observables.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp]
     L.hsc_scba.argtypes = [vp, i64, vp, dp, vp, vp, dp, dp, dp, i32, i32, vp, vp,
@@ -114,7 +116,8 @@ def load():
     L.hsc_destroy.argtypes = [vp]
     for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
                  "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile",
-                 "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_observables", "hsc_destroy",
+                 "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba",
+                 "hsc_set_contact_dense", "hsc_destroy",
                  "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
                  "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"):
         getattr(L, name).restype = ctypes.c_int
@@ -208,6 +211,10 @@ def hsc_scba(h, E, eta, sigma_r, sigma_less, d0, mix, tol, max_iter, precision, 
 
 def hsc_set_option(h, option, value):
     _check(h, load().hsc_set_option(h, int(option), int(value)))
+
+
+def hsc_set_contact_dense(h, contact, dense=True):
+    _check(h, load().hsc_set_contact_dense(h, int(contact), 1 if dense else 0))
 
 
 def hsc_get_option(h, option):

@@ -74,27 +74,22 @@ def test_rejects_bad_arguments_and_state():
     hsc.hsc_destroy(h)
 
 
-def _tree(dev, leaf, geometric=True, variant=0):
+def _tree(dev, leaf, geometric=True, variant=0, dense=()):
     h = _handle(dev, geometric)
     if variant:
         hsc.hsc_set_option(h, hsc.HSC_OPT_TREE_VARIANT, variant)
+    for c in dense:
+        hsc.hsc_set_contact_dense(h, c)
     st = hsc.hsc_analyze(h, leaf)
     cl = [hsc.hsc_cluster(h, i) for i in range(st.n_clusters)]
     hsc.hsc_destroy(h)
     return st, cl
 
 
-@pytest.mark.parametrize("dims,orb,leaf,geo", [((8, 8, 8), 1, 4, True), ((9, 5, 7), 1, 3, True),
-                                               ((6, 3, 2), 3, 2, True), ((7, 6, 5), 1, 2, False),
-                                               ((17, 1, 1), 1, 1, True)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
-def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo, variant):
-    """Every unknown is owned once; no H entry joins two unrelated clusters (separation); each U_i
-    is exactly the set of ancestor unknowns adjacent to the subtree of i (Section 2.2). Holds for
-    the plain tree and both alternate trees (cuts below the root shifted)."""
-    dev = W.cubic_device(dims, seed=1) if orb == 1 else W.wire_device(dims, orb=orb, seed=1)
-    st, cl = _tree(dev, leaf, geo, variant)
-    nc = st.n_clusters
+def _check_tree(dev, cl, extra_edges=()):
+    """Every unknown owned once; no coupling (H entries and extra_edges) joins two unrelated
+    clusters; each U_i is exactly the set of ancestor unknowns adjacent to the subtree of i."""
+    nc = len(cl)
     owner = np.full(dev.n, -1)
     for i, (info, own, upd) in enumerate(cl):
         assert np.all(owner[own] == -1)
@@ -112,11 +107,12 @@ def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo, variant
         for a in anc[i]:
             sub[a].add(i)
     H = dev.to_scipy().tocoo()
-    for a, b in zip(H.row, H.col):
+    pairs = list(zip(H.row, H.col)) + list(extra_edges)
+    for a, b in pairs:
         ca, cb = owner[a], owner[b]
         assert ca == cb or ca in anc[cb] or cb in anc[ca]
     adj = [set() for _ in range(dev.n)]
-    for a, b in zip(H.row, H.col):
+    for a, b in pairs:
         if a != b:
             adj[a].add(b)
     for i, (info, own, upd) in enumerate(cl):
@@ -128,8 +124,99 @@ def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo, variant
         assert set(upd.tolist()) == boundary
         assert all(owner[u] in anc[i] for u in upd)
         assert info.m == len(upd) and info.n == len(own)
+    return owner
+
+
+@pytest.mark.parametrize("dims,orb,leaf,geo", [((8, 8, 8), 1, 4, True), ((9, 5, 7), 1, 3, True),
+                                               ((6, 3, 2), 3, 2, True), ((7, 6, 5), 1, 2, False),
+                                               ((17, 1, 1), 1, 1, True)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_tree_partitions_and_update_sets_are_exact(dims, orb, leaf, geo, variant):
+    """Every unknown is owned once; no H entry joins two unrelated clusters (separation); each U_i
+    is exactly the set of ancestor unknowns adjacent to the subtree of i (Section 2.2). Holds for
+    the plain tree and both alternate trees (cuts below the root shifted)."""
+    dev = W.cubic_device(dims, seed=1) if orb == 1 else W.wire_device(dims, orb=orb, seed=1)
+    st, cl = _tree(dev, leaf, geo, variant)
+    _check_tree(dev, cl)
+    for i, (info, own, upd) in enumerate(cl):
         assert info.lesser == int(bool(np.isin(own, dev.contact_unknowns()).any()) or
                                   any(cl[c][0].lesser for c in info.child if c >= 0))
+
+
+def _dense_edges(dev, contacts):
+    """The coupling a DENSE self-energy block adds: every pair of unknowns of each contact."""
+    cu, cid = dev.contact_unknowns(), dev.contact_of_unknown()
+    out = []
+    for c in contacts:
+        u = cu[cid == c]
+        out += [(a, b) for a in u for b in u if a != b]
+    return out
+
+
+@pytest.mark.parametrize("dims,orb,leaf,geo,dense", [((8, 8, 8), 1, 4, True, (0, 1)),
+                                                     ((9, 5, 7), 1, 3, True, (0,)),
+                                                     ((6, 4, 4), 1, 2, True, (1,)),
+                                                     ((5, 3, 2), 2, 2, True, (0, 1)),
+                                                     ((7, 6, 5), 1, 2, False, (0, 1)),
+                                                     ((2, 3, 3), 1, 2, True, (0, 1))])
+@pytest.mark.parametrize("variant", [0, 2])
+def test_dense_contacts_become_one_cluster_each_on_top(dims, orb, leaf, geo, dense, variant):
+    """Section 3.1.2's DENSE self-energy couples all unknowns of a contact: with the contact marked
+    dense, its unknowns form one cluster, the dense contacts are chained at the top of the tree
+    (the last one is the root), and the tree stays exact for the graph with those couplings."""
+    dev = W.cubic_device(dims, seed=1) if orb == 1 else W.wire_device(dims, orb=orb, seed=1)
+    st, cl = _tree(dev, leaf, geo, variant, dense)
+    _check_tree(dev, cl, _dense_edges(dev, dense))
+    cu, cid = dev.contact_unknowns(), dev.contact_of_unknown()
+    nc = len(cl)
+    for k, c in enumerate(reversed(dense)):
+        info, own, upd = cl[nc - 1 - k]
+        assert set(own.tolist()) == set(cu[cid == c].tolist())
+        assert info.child[1] == -1
+
+
+def test_dense_end_faces_keep_the_geometric_interior_and_fill_the_interior_root():
+    """Both end planes of a cube dense: below them the interior box is dissected as before (its
+    root is the x = mid plane) and, after the interior is eliminated, that plane is coupled to both
+    faces: its update set is exactly the two faces."""
+    dims = (10, 6, 6)
+    dev = W.cubic_device(dims, seed=0)
+    st, cl = _tree(dev, 3, True, 0, (0, 1))
+    nc = len(cl)
+    inner = cl[nc - 3]
+    face = dims[1] * dims[2]
+    assert inner[0].parent == nc - 2 and cl[nc - 2][0].parent == nc - 1
+    xs = np.unique(inner[1] // face)
+    assert len(xs) == 1 and xs[0] == (1 + dims[0] - 2) // 2
+    assert inner[0].m == 2 * face and cl[nc - 2][0].m == face and cl[nc - 1][0].m == 0
+
+
+def test_a_dense_contact_that_is_not_an_end_plane_falls_back_to_graph_bisection():
+    dev = W.cubic_device((6, 5, 4), seed=2)
+    half = W.face_sites(dev.dims, 0)[:7]
+    dev2 = W.Device(dims=dev.dims, orb=1, rowptr=dev.rowptr, col=dev.col, val=dev.val,
+                    contact_ptr=np.array([0, len(half)], np.int64), contact_sites=half.astype(np.int32),
+                    gamma=np.array([0.5]))
+    st, cl = _tree(dev2, 2, True, 0, (0,))
+    _check_tree(dev2, cl, _dense_edges(dev2, (0,)))
+    assert set(cl[-1][1].tolist()) == set(half.tolist())
+
+
+def test_set_contact_dense_checks_arguments_and_requires_a_new_analysis():
+    dev = W.cubic_device((4, 4, 4), seed=0)
+    h = _handle(dev)
+    hsc.hsc_analyze(h, 2)
+    for c, v in ((2, 1), (-1, 1), (0, 2)):
+        with pytest.raises(hsc.HSCError) as ei:
+            hsc._check(h, hsc.load().hsc_set_contact_dense(h, c, v))
+        assert ei.value.code == hsc.HSC_ERR_ARG
+    hsc.hsc_set_contact_dense(h, 0)
+    sr, sl = W.self_energies(dev, 1)
+    out = np.zeros((1, dev.n), np.complex128)
+    with pytest.raises(hsc.HSCError) as ei:
+        hsc.hsc_solve(h, np.array([0.1]), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(), None, None)
+    assert ei.value.code == hsc.HSC_ERR_STATE
+    hsc.hsc_destroy(h)
 
 
 @pytest.mark.parametrize("dims,leaf,geo", [((32, 32, 32), 8, True), ((12, 9, 7), 3, True),
@@ -156,6 +243,23 @@ def test_operation_count_follows_table_1_cube_slope():
         f.append(st.flops_gr + st.flops_gl)
     slope = np.polyfit(np.log(Ns), np.log(f), 1)[0]
     assert 5.3 < slope < 6.5, slope
+
+
+def test_dense_contacts_keep_the_cube_slope():
+    """Section 3.1.2: DENSE self-energies make the HSC-extension slower but leave its asymptotic
+    operation count unchanged. With both end planes dense the model's log-log slope between N = 24
+    and N = 40 stays near 6, at a bounded multiple of the diagonal case."""
+    Ns = [24, 32, 40]
+    f, g = [], []
+    for N in Ns:
+        dev = W.cubic_device((N, N, N), seed=0)
+        st, _ = _tree(dev, 8)
+        st_d, _ = _tree(dev, 8, dense=(0, 1))
+        f.append(st.flops_gr + st.flops_gl)
+        g.append(st_d.flops_gr + st_d.flops_gl)
+    slope = np.polyfit(np.log(Ns), np.log(g), 1)[0]
+    assert 5.3 < slope < 6.5, slope
+    assert all(1.2 < b / a < 3.0 for a, b in zip(f, g))
 
 
 def test_degenerate_chain_tree():
