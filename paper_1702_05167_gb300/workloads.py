@@ -133,6 +133,31 @@ def cubic_device(dims, t=-1.0, W=1.0, seed=0, gamma=0.5):
                   meta=dict(kind="cubic", t=t, W=W, seed=seed, onsite=eps))
 
 
+def magnetic_cubic_device(dims, phi, t=-1.0, W=1.0, seed=0, gamma=0.5):
+    """cubic_device in a uniform magnetic field along z: Peierls phases in the Landau gauge
+    A = (0, B x, 0), so the hopping from (x, y, z) to (x, y+1, z) is t exp(2 pi i phi x) (phi: flux
+    per plaquette in flux quanta) and the reverse hopping its conjugate. H is Hermitian and, unless
+    2 phi is an integer, not symmetric. Onsite energies and contacts as cubic_device(dims, t, W,
+    seed, gamma)."""
+    import scipy.sparse as sp
+    base = cubic_device(dims, t=t, W=W, seed=seed, gamma=gamma)
+    Nx, Ny, Nz = base.dims
+    H = base.to_scipy().tolil()
+    for x in range(Nx):
+        ph = t * np.exp(2j * np.pi * phi * x)
+        for y in range(Ny - 1):
+            for z in range(Nz):
+                a, b = site_index(x, y, z, base.dims), site_index(x, y + 1, z, base.dims)
+                H[a, b] = ph
+                H[b, a] = np.conj(ph)
+    M = sp.csr_matrix(H)
+    M.sort_indices()
+    return Device(dims=base.dims, orb=1, rowptr=M.indptr.astype(np.int64), col=M.indices.astype(np.int32),
+                  val=M.data.astype(np.complex128), contact_ptr=base.contact_ptr,
+                  contact_sites=base.contact_sites, gamma=base.gamma,
+                  meta=dict(base.meta, kind="magnetic", phi=phi))
+
+
 def wire_device(dims, orb=10, seed=0, onsite_range=8.0, hop_fro=2.0, gamma=0.6):
     """Multi-orbital wire: random real-symmetric onsite blocks Q diag(U[-r, r]) Q^T per site and one
     random hopping block per bond direction scaled to Frobenius norm `hop_fro` (reverse bond gets the
