@@ -140,6 +140,25 @@ int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta,
               hsc_c128* diag_gr, hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl,
               void* cuda_stream, int32_t io_on_device);
 
+/* hsc_solve_dense -- hsc_solve with DENSE contact self-energy blocks (Section 3.1.2) added.
+ *   Needs at least one contact marked with hsc_set_contact_dense before hsc_analyze.
+ *   dense_r[n_E][n_dense]   per energy, the blocks of the dense contacts in contact order, each
+ *                           nu x nu row-major over the contact's unknowns in slot order (nu = its
+ *                           sites x orb; n_dense = sum of nu^2). Sigma^r = diag(sigma_r) + blocks.
+ *   dense_less[n_E][n_dense] the same for Sigma^< (anti-Hermitian, as i f Gamma); required exactly
+ *                           when sigma_less is given
+ *   Everything else as hsc_solve (dense_* on the device when io_on_device = 1; with host I/O they
+ *   are staged on the device whole). The blocks are complex symmetric for a lead Hamiltonian that
+ *   is (Sigma^r = tau g_s tau^T). No residual record and no re-solve: the residual kernel handles
+ *   diagonal self-energies only, so hsc_residual is not defined after this call.
+ *   Not yet run on a GB300 (the kernel adding the blocks, k_add_dense, is compiled and reviewed).
+ *   Errors: as hsc_solve; HSC_ERR_ARG when no contact is dense or the block arrays are missing. */
+int hsc_solve_dense(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                    const hsc_c128* sigma_less, const hsc_c128* dense_r, const hsc_c128* dense_less,
+                    int32_t precision, int32_t n_req, const int32_t* req_pairs, hsc_c128* diag_gr,
+                    hsc_c128* diag_gl, hsc_c128* req_gr, hsc_c128* req_gl, void* cuda_stream,
+                    int32_t io_on_device);
+
 /* Options of a handle (hsc_set_option / hsc_get_option). Setting one discards the handle's device
  * schedule and workspace (rebuilt by the next solve). HSC_OPT_LEAF is read-only (the leaf_max of
  * the last hsc_analyze). */

@@ -238,6 +238,22 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
     }
   for (int64_t s = 0; s < ns; ++s)
     if (P.site_cluster[s] < 0) return "site not assigned";
+  for (int c : dense_c) {
+    Plan::Dense D;
+    D.contact = c;
+    D.cluster = P.site_cluster[in.contact_sites[in.contact_ptr[c]]];
+    D.nu = (in.contact_ptr[c + 1] - in.contact_ptr[c]) * orb;
+    D.blk = P.dense_elems;
+    D.loc = (int64_t)P.dense_local.size();
+    for (int64_t k = in.contact_ptr[c]; k < in.contact_ptr[c + 1]; ++k) {
+      const int s = in.contact_sites[k];
+      if (P.site_cluster[s] != D.cluster) return "a dense contact is split over clusters";
+      for (int o = 0; o < orb; ++o) P.dense_local.push_back(P.site_local[s] * orb + o);
+    }
+    if ((int64_t)cl[D.cluster].sites.size() * orb != D.nu) return "a dense contact shares its cluster";
+    P.dense_elems += D.nu * D.nu;
+    P.dense.push_back(D);
+  }
   for (int i = 0; i < nc; ++i) {
     cl[i].first_desc = i;
     cl[i].height = 0;

@@ -86,6 +86,14 @@ struct LevelCluster {
   int64_t elem_start;    // flattened element prefix inside the level (kernel-specific)
 };
 
+// A DENSE contact's self-energy block (Section 3.1.2) and where it goes: the owner cluster's front
+// (offset aug, row length ld = n + m), nu x nu values at offset blk of each energy's block array,
+// the local row of slot k at loc[k].
+struct DenseBlock {
+  int64_t aug = 0, blk = 0, loc = 0;
+  int32_t ld = 0, nu = 0, lesser = 0;
+};
+
 struct ClusterGlobal {   // per-cluster data needed when another cluster reads this one's blocks
   int n, m, depth, lesser;
   int64_t aug, sq;

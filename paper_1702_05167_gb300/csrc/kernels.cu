@@ -523,6 +523,25 @@ __global__ void k_observables(int64_t n, const c64* gr, const c64* gl, const c64
   }
 }
 
+// ---- DENSE contact self-energies (Section 3.1.2): A_ii -= Sigma^r block and, for the lesser
+//      front, L_ii += Sigma^< block on the own rows of each dense contact's cluster; runs after the
+//      diagonal terms and before the cluster's Gauss-Jordan. Distinct (a, b) hit distinct front
+//      entries (loc is a permutation of the cluster's rows), so there are no races.
+__global__ void k_add_dense(const DenseBlock* db, const int32_t* loc, const c64* dr, const c64* dl,
+                            int64_t des, c64* F, c64* L, int64_t aug_es, int ne) {
+  const DenseBlock& B = db[blockIdx.y];
+  const int64_t nn = (int64_t)B.nu * B.nu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = k / B.nu, b = k - a * B.nu;
+    const int64_t dst = B.aug + (int64_t)loc[B.loc + a] * B.ld + loc[B.loc + b];
+    for (int e = 0; e < ne; ++e) {
+      F[e * aug_es + dst] = csub(F[e * aug_es + dst], dr[e * des + B.blk + k]);
+      if (dl && B.lesser) L[e * aug_es + dst] = cadd(L[e * aug_es + dst], dl[e * des + B.blk + k]);
+    }
+  }
+}
+
 // ---- self-consistent dephasing (the scattering part of Sigma^r in Eq. 1, local elastic model):
 //      on every contact slot k of energy e, with u its unknown, F^r = d0 G^r_uu and F^< = i d0 Im G^<_uu
 //      (G^< is anti-Hermitian, Algorithm 2: a real part of its diagonal is rounding error, and fed
@@ -563,6 +582,15 @@ __global__ void k_scba_mix(int64_t total, int64_t n, int64_t ncs, const int64_t*
 }
 
 }  // namespace
+
+cudaError_t launch_add_dense(const DenseBlock* db, int nb, int64_t max_nn, const int32_t* loc,
+                             const c64* dr, const c64* dl, int64_t des, c64* F, c64* L, int64_t aug_es,
+                             int ne, cudaStream_t s) {
+  if (nb <= 0 || max_nn <= 0) return cudaSuccess;
+  const int64_t bx = std::min<int64_t>((max_nn + 255) / 256, 1024);
+  k_add_dense<<<dim3((unsigned)bx, (unsigned)nb), 256, 0, s>>>(db, loc, dr, dl, des, F, L, aug_es, ne);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scba_mix(int64_t n_E, int64_t n, int64_t ncs, const int64_t* slot_unknown,
                             const c64* gr, const c64* gl, const c64* cr, const c64* cl, double d0,

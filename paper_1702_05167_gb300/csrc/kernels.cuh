@@ -35,6 +35,10 @@ cudaError_t launch_out(const int64_t* doff, int64_t n, const int64_t* poff, int6
                        const c64* G, const c64* P, int64_t aug_es, c64* ogr, c64* ogl, c64* pgr,
                        c64* pgl, int ne, cudaStream_t s);
 
+cudaError_t launch_add_dense(const DenseBlock* db, int nb, int64_t max_nn, const int32_t* loc,
+                             const c64* dr, const c64* dl, int64_t des, c64* F, c64* L, int64_t aug_es,
+                             int ne, cudaStream_t s);
+
 cudaError_t launch_scba_mix(int64_t n_E, int64_t n, int64_t ncs, const int64_t* slot_unknown,
                             const c64* gr, const c64* gl, const c64* cr, const c64* cl, double d0,
                             double mix, c64* s_r, c64* s_l, c64* sig_r, c64* sig_l,

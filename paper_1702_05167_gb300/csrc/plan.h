@@ -65,6 +65,18 @@ struct Plan {
   std::vector<int64_t> iperm;     // [n]  unknown -> (cluster, local) via cluster_of_unknown/local
   std::vector<int32_t> unk_cluster, unk_local;   // [n]
 
+  // DENSE contacts (Section 3.1.2), in contact order: the cluster that owns all of the contact's
+  // unknowns, their number, the block's offset in a per-energy dense self-energy array (blocks
+  // nu x nu row-major in the contact's slot order, contact after contact) and, from `loc`, the
+  // local row inside that cluster of each slot's unknown (dense_local)
+  struct Dense {
+    int contact = -1, cluster = -1;
+    int64_t nu = 0, blk = 0, loc = 0;
+  };
+  std::vector<Dense> dense;
+  std::vector<int32_t> dense_local;
+  int64_t dense_elems = 0;
+
   // ---- model ----
   double flops_gr = 0, flops_gl = 0;   // real flops per energy (complex MAC = 8)
 };

@@ -43,6 +43,8 @@ struct UpLevel {
   int64_t gj = 0;           // index into the GJProb array
   int nmat = 0;
   std::vector<GemmPair> steps;
+  int dense0 = 0, dense_n = 0;   // DENSE contact blocks of this level's clusters (dense_dev range)
+  int64_t dense_max = 0;         // largest nu^2 among them
 };
 
 struct DownLevel {
@@ -123,6 +125,11 @@ struct DeviceState {
   void* io = nullptr;
   int64_t* poff = nullptr;
   int64_t pair_cap = 0;
+  DenseBlock* dense_dev = nullptr;   // DENSE contact blocks, grouped by upward level
+  int32_t* dense_loc = nullptr;      // their slot -> local row maps
+  const c64* dense_r = nullptr;      // set by hsc_solve_dense for one call: per-energy blocks,
+  const c64* dense_l = nullptr;      //   stride dense_es elements; dense_e0 = the wave's first energy
+  int64_t dense_es = 0, dense_e0 = 0;
   int64_t* slot_unknown = nullptr;   // contact slot -> unknown (observables)
   int32_t* slot_contact = nullptr;   // contact slot -> contact id
   cudaStream_t branch = nullptr;
@@ -581,6 +588,29 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->res_rowptr, h->rowptr);
   UP(&d->res_loc, rloc);
   UP(&d->unk_slot, uslot);
+  {
+    // DENSE contact blocks grouped by the upward level of their cluster
+    std::vector<DenseBlock> db;
+    for (size_t hl = 0; hl < d->up.size(); ++hl) {
+      UpLevel& U = d->up[hl];
+      U.dense0 = (int)db.size();
+      for (const auto& D : P.dense) {
+        if (P.cl[D.cluster].height != (int)hl) continue;
+        DenseBlock b;
+        b.aug = P.off[D.cluster].aug;
+        b.blk = D.blk;
+        b.loc = D.loc;
+        b.ld = (int32_t)(P.cl[D.cluster].n + P.cl[D.cluster].m);
+        b.nu = (int32_t)D.nu;
+        b.lesser = P.cl[D.cluster].lesser ? 1 : 0;
+        db.push_back(b);
+        U.dense_max = std::max<int64_t>(U.dense_max, D.nu * D.nu);
+      }
+      U.dense_n = (int)db.size() - U.dense0;
+    }
+    UP(&d->dense_dev, db);
+    UP(&d->dense_loc, P.dense_local);
+  }
 #undef UP
   if ((e = cudaMalloc((void**)&d->flag, 4 * sizeof(int))) != cudaSuccess)
     return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc flag");
@@ -741,6 +771,12 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
     LAUNCH(K_ADD_A, 2, 0.0, 0.0,
            launch_add_a(lc, U.nl, U.max_h, U.max_n, d->h_rq, d->h_vi, d->hval, d->own_contact, E,
                         eta, sr, sl, ncs, d->F, d->L, d->aug_es, ne, s));
+    if (d->dense_r && U.dense_n > 0)
+      LAUNCH(K_ADD_A, 1, 0.0, 0.0,
+             launch_add_dense(d->dense_dev + U.dense0, U.dense_n, U.dense_max, d->dense_loc,
+                              d->dense_r + d->dense_e0 * d->dense_es,
+                              (les && d->dense_l) ? d->dense_l + d->dense_e0 * d->dense_es : nullptr,
+                              d->dense_es, d->F, d->L, d->aug_es, ne, s));
     // Gauss-Jordan inversion of A_ii in place (D_i^{-1}), panel by panel
     const GJProb* gp = d->gjp + U.gj;
     for (size_t st = 0; st < U.steps.size(); ++st) {
@@ -794,7 +830,7 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
     GEMM(D.d[8], d->X, d->x_es, d->P, d->aug_es, d->P, d->aug_es, d->P, d->aug_es);
   }
 #undef GEMM
-  if (d->resid_wave)
+  if (d->resid_wave && !d->dense_r)   // the residual kernel knows diagonal self-energies only
     LAUNCH(K_RESID, 1, 0.0, 0.0,
            launch_residual(h->n, d->res_rowptr, d->hval, d->res_loc, d->doff, d->unk_slot, E, eta, sr,
                            ncs, d->G, d->aug_es, d->resid_wave, ne, s));
@@ -1017,6 +1053,7 @@ int enqueue_device(hsc_ctx* h, int64_t n_E, int64_t wave, const double* E, doubl
     const int ne = (int)std::min<int64_t>(wave, n_E - e0);
     d->growth_wave = d->growth + e0;
     d->resid_wave = d->resid + e0;
+    d->dense_e0 = e0;
     const c64* dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
     const c64* dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
     c64* ogr = reinterpret_cast<c64*>(diag_gr) + e0 * n;
@@ -1208,6 +1245,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
       const int ne = (int)std::min<int64_t>(wave, n_E - e0);
       d->growth_wave = d->growth + e0;
       d->resid_wave = d->resid + e0;
+      d->dense_e0 = e0;
       CK(cudaMemcpyAsync(sE, E + e0, ne * 8, cudaMemcpyHostToDevice, s));
       if (ncs > 0) {
         CK(cudaMemcpyAsync(ssr, sigma_r + e0 * ncs, ne * ncs * 16, cudaMemcpyHostToDevice, s));
@@ -1225,7 +1263,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
     }
   }
   if ((rc = read_flags(h, s)) != HSC_OK) return rc;
-  if (h->opt_resolve > 0 && !h->is_alt && precision == HSC_FP64)
+  if (h->opt_resolve > 0 && !h->is_alt && precision == HSC_FP64 && !d->dense_r)
     for (int v = 1; v <= 4; ++v)
       if (v != h->nd_variant &&
           (rc = hsc::resolve_grown(v, h, n_E, E, eta, sigma_r, sigma_less, precision, n_req, req_pairs,
@@ -1233,6 +1271,56 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
         return rc;
   h->err.clear();
   return HSC_OK;
+}
+
+extern "C" int hsc_solve_dense(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,
+                               const hsc_c128* sigma_less, const hsc_c128* dense_r,
+                               const hsc_c128* dense_less, int32_t precision, int32_t n_req,
+                               const int32_t* req_pairs, hsc_c128* diag_gr, hsc_c128* diag_gl,
+                               hsc_c128* req_gr, hsc_c128* req_gl, void* cuda_stream,
+                               int32_t io_on_device) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (!h->analyzed) return hsc_fail(h, HSC_ERR_STATE, "hsc_analyze has not run");
+  const hsc::Plan& P = h->plan;
+  if (P.dense.empty())
+    return hsc_fail(h, HSC_ERR_ARG, "no contact is dense (hsc_set_contact_dense, then hsc_analyze)");
+  if (n_E < 0 || (n_E > 0 && !dense_r) || (sigma_less != nullptr) != (dense_less != nullptr))
+    return hsc_fail(h, HSC_ERR_ARG, "dense_r is required; dense_less goes with sigma_less");
+  if (n_E == 0)
+    return hsc_solve(h, n_E, E, eta, sigma_r, sigma_less, precision, n_req, req_pairs, diag_gr, diag_gl,
+                     req_gr, req_gl, cuda_stream, io_on_device);
+  int rc = get_state(h);
+  if (rc != HSC_OK) return rc;
+  hsc::DeviceState* d = h->dev;
+  const int64_t des = P.dense_elems;
+  struct Tmp {
+    void* p = nullptr;
+    ~Tmp() { if (p) cudaFree(p); }
+  } tmp;
+  const hsc::c64* dr = reinterpret_cast<const hsc::c64*>(dense_r);
+  const hsc::c64* dl = reinterpret_cast<const hsc::c64*>(dense_less);
+  if (!io_on_device) {   // the blocks go to the device whole; the rest follows hsc_solve's staging
+    const size_t one = (size_t)n_E * des * 16;
+    if (cudaMalloc(&tmp.p, dense_less ? 2 * one : one) != cudaSuccess) {
+      tmp.p = nullptr;
+      cudaGetLastError();
+      return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc dense self-energy staging");
+    }
+    if (cudaMemcpy(tmp.p, dense_r, one, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (dense_less && cudaMemcpy((char*)tmp.p + one, dense_less, one, cudaMemcpyHostToDevice) != cudaSuccess))
+      return hsc_fail(h, HSC_ERR_CUDA, "copy dense self-energies");
+    dr = reinterpret_cast<const hsc::c64*>(tmp.p);
+    dl = dense_less ? reinterpret_cast<const hsc::c64*>((char*)tmp.p + one) : nullptr;
+  }
+  d->dense_r = dr;
+  d->dense_l = dl;
+  d->dense_es = des;
+  d->dense_e0 = 0;
+  rc = hsc_solve(h, n_E, E, eta, sigma_r, sigma_less, precision, n_req, req_pairs, diag_gr, diag_gl, req_gr,
+                 req_gl, cuda_stream, io_on_device);
+  d->dense_r = nullptr;
+  d->dense_l = nullptr;
+  return rc;
 }
 
 extern "C" int hsc_debug_offset(hsc_t h, int32_t i, int64_t* aug, int64_t* sq, int64_t* x) {

@@ -18,7 +18,8 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
           8: "HSC_ERR_TIMEOUT"}
 
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
-           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_set_contact_dense", "hsc_profile",
+           "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_set_contact_dense", "hsc_solve_dense",
+           "hsc_profile",
            "hsc_profile_read", "hsc_growth",
            "hsc_residual",
            "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba", "hsc_last_error", "hsc_destroy",
@@ -94,6 +95,7 @@ def load():
                            ctypes.POINTER(hsc_tune_result)]
     L.hsc_set_option.argtypes = [vp, i32, i32]
     L.hsc_set_contact_dense.argtypes = [vp, i32, i32]
+    L.hsc_solve_dense.argtypes = [vp, i64, vp, dp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, i32]
     L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
     L.hsc_observables.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp]
     L.hsc_scba.argtypes = [vp, i64, vp, dp, vp, vp, dp, dp, dp, i32, i32, vp, vp,
@@ -117,7 +119,7 @@ def load():
     for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
                  "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile",
                  "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba",
-                 "hsc_set_contact_dense", "hsc_destroy",
+                 "hsc_set_contact_dense", "hsc_solve_dense", "hsc_destroy",
                  "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
                  "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"):
         getattr(L, name).restype = ctypes.c_int
@@ -207,6 +209,21 @@ def hsc_scba(h, E, eta, sigma_r, sigma_less, d0, mix, tol, max_iter, precision, 
                            1 if io_on_device else 0)
     _check(h, code)
     return it.value, dl.value
+
+
+def hsc_solve_dense(h, E, eta, sigma_r, sigma_less, dense_r, dense_less, precision, req_pairs, diag_gr,
+                    diag_gl, req_gr, req_gl, stream=None, io_on_device=False):
+    """Marshal buffers to hsc_solve_dense (as hsc_solve, plus the dense contact blocks)."""
+    pairs = None
+    n_req = 0
+    if req_pairs is not None and len(req_pairs):
+        pairs = np.ascontiguousarray(req_pairs, dtype=np.int32)
+        n_req = pairs.shape[0]
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(h, load().hsc_solve_dense(h, int(E.shape[0]), _ptr(E), float(eta), _ptr(sigma_r),
+                                     _ptr(sigma_less), _ptr(dense_r), _ptr(dense_less), int(precision),
+                                     n_req, _ptr(pairs), _ptr(diag_gr), _ptr(diag_gl), _ptr(req_gr),
+                                     _ptr(req_gl), s, 1 if io_on_device else 0))
 
 
 def hsc_set_option(h, option, value):

@@ -245,6 +245,32 @@ def test_operation_count_follows_table_1_cube_slope():
     assert 5.3 < slope < 6.5, slope
 
 
+def test_solve_dense_checks_its_arguments_on_the_host():
+    """hsc_solve_dense needs a dense contact in the analysed tree and the block arrays that go with
+    the diagonal ones; all checked before any device work."""
+    dev = W.cubic_device((4, 3, 3), seed=0)
+    sr, sl = W.self_energies(dev, 1)
+    out = np.zeros((1, dev.n), np.complex128)
+    E = np.array([0.2])
+    blk = np.zeros((1, 2 * 9 * 9), np.complex128)
+    h = _handle(dev)
+    hsc.hsc_analyze(h, 2)
+    with pytest.raises(hsc.HSCError) as ei:     # no dense contact
+        hsc.hsc_solve_dense(h, E, 1e-6, sr, sl, blk, blk, hsc.HSC_FP64, None, out, out.copy(), None, None)
+    assert ei.value.code == hsc.HSC_ERR_ARG and "dense" in str(ei.value)
+    hsc.hsc_set_contact_dense(h, 0)
+    hsc.hsc_set_contact_dense(h, 1)
+    with pytest.raises(hsc.HSCError) as ei:     # not analysed since
+        hsc.hsc_solve_dense(h, E, 1e-6, sr, sl, blk, blk, hsc.HSC_FP64, None, out, out.copy(), None, None)
+    assert ei.value.code == hsc.HSC_ERR_STATE
+    hsc.hsc_analyze(h, 2)
+    for r, l, lsig in ((None, blk, sl), (blk, None, sl), (blk, blk, None)):
+        with pytest.raises(hsc.HSCError) as ei:
+            hsc.hsc_solve_dense(h, E, 1e-6, sr, lsig, r, l, hsc.HSC_FP64, None, out, out.copy(), None, None)
+        assert ei.value.code == hsc.HSC_ERR_ARG
+    hsc.hsc_destroy(h)
+
+
 def test_dense_contacts_keep_the_cube_slope():
     """Section 3.1.2: DENSE self-energies make the HSC-extension slower but leave its asymptotic
     operation count unchanged. With both end planes dense the model's log-log slope between N = 24
