@@ -50,6 +50,9 @@ def parse():
                    help="precision of the batch8 workload")
     p.add_argument("--energies", type=int, default=0,
                    help="solve only this many of the workload's energies (every k-th; 0: all)")
+    p.add_argument("--ordering", default="geometric", choices=["geometric", "graph"],
+                   help="nested dissection of the main solve: geometric planes (default) or "
+                        "breadth-first level-set bisection of the site graph (HSC_OPT_ORDERING = 1)")
     p.add_argument("--workload", default="cubic32", choices=["cubic32", "cubic24x8E", "batch8", "wire"],
                    help="cubic32: the metric workload; cubic24x8E: 24^3 grid, 8 energies (a few GB, "
                         "for ncu captures)")
@@ -186,7 +189,8 @@ def run_hsc(args):
     pairs = cfg.get("pairs")
     if pairs is None:
         pairs = np.zeros((0, 2), dtype=np.int32)
-    solver = hsc.Solver(dev, cfg["leaf"])
+    geometric = args.ordering == "geometric"
+    solver = hsc.Solver(dev, cfg["leaf"], geometric)
     st = solver.stats
     h = solver.h
     n = dev.n
@@ -427,7 +431,7 @@ def run_hsc(args):
     # ---- secondary: the plain separator tree only (no residual-driven re-solve) ----
     plain = None
     if rank == 0 and not args.no_plain:
-        sp = hsc.Solver(dev, cfg["leaf"])
+        sp = hsc.Solver(dev, cfg["leaf"], geometric)
         hsc.hsc_set_option(sp.h, hsc.HSC_OPT_RESOLVE_DIGITS, 0)
         def step_p():
             hsc.hsc_solve(sp.h, tE, cfg["eta"], tsr, tsl, hsc.HSC_FP64, pairs, ogr2, ogl2, pgr2, pgl2,
@@ -473,6 +477,7 @@ def run_hsc(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
                 "config": {"workload": cfg["name"], "grid": list(dev.dims),
                            "energies_per_gpu": nE, "eta": cfg["eta"], "leaf_max": cfg["leaf"],
+                           "ordering": args.ordering,
                            "precision": "complex128 (HSC_FP64)", "io": "device-resident",
                            "fp64_engine": "per product list by cost model: FP64 tensor pipe or FP64 "
                                           "emulation on the BF16 tensor cores (HSC_OPT_FP64_ENGINE = 0)",

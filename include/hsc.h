@@ -187,8 +187,13 @@ typedef enum {
                               /* Each alternate tree is analysed on first need and works in the */
                               /* handle's own workspace after the first pass.                   */
                               /* hsc_solve_batch does not re-solve.                             */
-  HSC_OPT_TREE_VARIANT = 8    /* 1..4: the next hsc_analyze builds that alternate separator     */
+  HSC_OPT_TREE_VARIANT = 8,   /* 1..4: the next hsc_analyze builds that alternate separator     */
                               /* tree itself (0, default: the plain tree)                       */
+  HSC_OPT_ORDERING = 9        /* 1: the next hsc_analyze uses breadth-first level-set bisection */
+                              /* of the site graph even when grid_dims were given (its level     */
+                              /* sets from a corner are diagonal planes: on a 32^3 cube the     */
+                              /* model counts 260 instead of 369 GFLOP per energy, on 24^3 more)*/
+                              /* 0 (default): geometric dissection when grid_dims were given    */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);

@@ -115,6 +115,7 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   in.contact_ptr = h->contact_ptr.data();
   in.contact_sites = h->contact_sites.data();
   std::memcpy(in.dims, h->dims, sizeof(in.dims));
+  if (h->opt_ordering == 1) in.dims[0] = in.dims[1] = in.dims[2] = 0;   // graph bisection
   in.variant = h->nd_variant;
   in.contact_dense = h->contact_dense.empty() ? nullptr : h->contact_dense.data();
   hsc_drop_alt(h);   // the twin follows the leaf size of this analysis
@@ -203,6 +204,10 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       if (value < 0 || value > 4 || h->is_alt) return hsc_fail(h, HSC_ERR_ARG, "tree variant must be in [0, 4]");
       h->nd_variant = value;
       break;
+    case HSC_OPT_ORDERING:
+      if (value < 0 || value > 1) return hsc_fail(h, HSC_ERR_ARG, "ordering must be 0 or 1");
+      h->opt_ordering = value;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
@@ -223,6 +228,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_FP64_ENGINE: *value = h->opt_fp64_engine; break;
     case HSC_OPT_RESOLVE_DIGITS: *value = h->opt_resolve; break;
     case HSC_OPT_TREE_VARIANT: *value = h->nd_variant; break;
+    case HSC_OPT_ORDERING: *value = h->opt_ordering; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   return HSC_OK;
@@ -276,6 +282,7 @@ hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
   a->opt_gj_fp64 = h->opt_gj_fp64;
   a->opt_4m = h->opt_4m;
   a->opt_fp64_engine = h->opt_fp64_engine;
+  a->opt_ordering = h->opt_ordering;
   a->nd_variant = v;
   a->is_alt = true;
   if (hsc_analyze(a, h->leaf_max, nullptr) != HSC_OK) {

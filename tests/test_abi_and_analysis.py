@@ -288,6 +288,26 @@ def test_dense_contacts_keep_the_cube_slope():
     assert all(1.2 < b / a < 3.0 for a, b in zip(f, g))
 
 
+def test_graph_ordering_option_matches_a_handle_without_grid_dims():
+    """HSC_OPT_ORDERING = 1 makes the next analysis ignore grid_dims: the same tree as a handle
+    created without them, and exact for any variant."""
+    dev = W.cubic_device((9, 8, 7), seed=3)
+    h = _handle(dev, True)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_ORDERING) == 0
+    hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 1)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_ORDERING) == 1
+    st = hsc.hsc_analyze(h, 2)
+    cl = [hsc.hsc_cluster(h, i) for i in range(st.n_clusters)]
+    with pytest.raises(hsc.HSCError) as ei:
+        hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 2)
+    assert ei.value.code == hsc.HSC_ERR_ARG
+    hsc.hsc_destroy(h)
+    st2, cl2 = _tree(dev, 2, geometric=False)
+    assert st.n_clusters == st2.n_clusters and st.flops_gr == st2.flops_gr
+    assert all(np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]) for a, b in zip(cl, cl2))
+    _check_tree(dev, cl)
+
+
 def test_degenerate_chain_tree():
     """A 1D chain with leaves of one site: every cluster is one unknown and every update set has at
     most two entries (the separator structure that makes HSC coincide with RGF, Section 2.2)."""
