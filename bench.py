@@ -161,7 +161,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
-            "config": {"workload": "cubic_32x32x32_64E (W=1 eV, eta=1e-6, contacts x=0/x=31)",
+            "config": {"workload": cfg["name"], "grid": list(cfg["dev"].dims),
+                       "energies_per_gpu": len(cfg["energies"]), "eta": cfg["eta"],
+                       "device": "W = 1 eV, contacts on x = 0 and x = 31",
                        "oracle": "RGF sweep along x, complex128, numpy/OpenBLAS",
                        "step": "one energy of the 64-energy grid (bounded sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
