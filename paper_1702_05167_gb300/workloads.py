@@ -158,6 +158,55 @@ def magnetic_cubic_device(dims, phi, t=-1.0, W=1.0, seed=0, gamma=0.5):
                   meta=dict(base.meta, kind="magnetic", phi=phi))
 
 
+def gbng_device(nx, ny, nz, t=-2.7, t_perp=0.35, delta_bn=2.0, W=0.0, seed=0, gamma=1.0):
+    """Synthetic stand-in for the graphene - hBN - graphene stack of Section 3.2 (p_z orbitals).
+
+    nz honeycomb layers of nx x ny sites, each in brick-wall form: bonds (x, y)-(x+1, y), and
+    (x, y)-(x, y+1) where x + y + z is even (three in-plane neighbours in the bulk). The outer two
+    layers are graphene (onsite 0), the inner ones hBN (onsite +delta_bn on the x + y + z even
+    sublattice, -delta_bn on the other). AB (Bernal) stacking: site (x, y, z) couples to
+    (x, y, z+1) with t_perp where x + y + z is even, so half the sites of a layer have a partner in
+    each neighbouring layer. Onsite disorder uniform in [-W/2, W/2]. Contacts (wide-band,
+    broadening gamma): the top layer's row y = 0 and the bottom layer's row y = ny-1, where the
+    paper's semi-infinite ribbon electrodes attach. Sites are numbered (y * nz + z) * nx + x, so
+    grid_dims (ny, nz, nx) describe the same grid and the y-slices are RGF layers.
+    Parameters are synthetic choices (the paper takes them from its reference).
+    """
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    dims = (int(ny), int(nz), int(nx))
+    n = ny * nz * nx
+    idx = lambda x, y, z: (y * nz + z) * nx + x
+    rows, cols, vals = [], [], []
+    def bond(a, b, v):
+        rows.extend([a, b]); cols.extend([b, a]); vals.extend([v, v])
+    eps = rng.uniform(-W / 2, W / 2, size=n) if W > 0 else np.zeros(n)
+    for z in range(nz):
+        bn = 0 < z < nz - 1
+        for y in range(ny):
+            for x in range(nx):
+                a = idx(x, y, z)
+                if bn:
+                    eps[a] += delta_bn if (x + y + z) % 2 == 0 else -delta_bn
+                if x + 1 < nx:
+                    bond(a, idx(x + 1, y, z), t)
+                if y + 1 < ny and (x + y + z) % 2 == 0:
+                    bond(a, idx(x, y + 1, z), t)
+                if z + 1 < nz and (x + y + z) % 2 == 0:
+                    bond(a, idx(x, y, z + 1), t_perp)
+    rows.extend(range(n)); cols.extend(range(n)); vals.extend(eps.tolist())
+    M = sp.coo_matrix((np.asarray(vals, dtype=np.complex128), (rows, cols)), shape=(n, n)).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    left = np.array([idx(x, 0, nz - 1) for x in range(nx)], dtype=np.int32)
+    right = np.array([idx(x, ny - 1, 0) for x in range(nx)], dtype=np.int32)
+    return Device(dims=dims, orb=1, rowptr=M.indptr.astype(np.int64), col=M.indices.astype(np.int32),
+                  val=M.data.astype(np.complex128),
+                  contact_ptr=np.array([0, nx, 2 * nx], dtype=np.int64),
+                  contact_sites=np.concatenate([left, right]).astype(np.int32),
+                  gamma=np.array([gamma, gamma]), meta=dict(kind="gbng", onsite=eps))
+
+
 def wire_device(dims, orb=10, seed=0, onsite_range=8.0, hop_fro=2.0, gamma=0.6):
     """Multi-orbital wire: random real-symmetric onsite blocks Q diag(U[-r, r]) Q^T per site and one
     random hopping block per bond direction scaled to Frobenius norm `hop_fro` (reverse bond gets the

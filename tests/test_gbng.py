@@ -1,0 +1,61 @@
+"""The graphene - hBN - graphene stand-in (Section 3.2's layered, non-cubic sparsity): structure,
+exact trees under both orderings, the operation-count slope against RGF's, and the oracle's RGF
+along y against the dense definition. CPU only."""
+import numpy as np
+import pytest
+
+from oracle import dense, rgf
+from paper_1702_05167_gb300 import hsc, workloads as W
+from test_abi_and_analysis import _check_tree, _tree
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    hsc.load()
+
+
+def test_structure_is_a_bernal_stack_of_honeycomb_layers():
+    dev = W.gbng_device(10, 8, 5, seed=1)
+    H = dev.to_scipy().toarray()
+    assert np.array_equal(H, H.T) and np.abs(H.imag).max() == 0
+    deg = (np.abs(H) > 0).sum(axis=1) - 1
+    assert deg.max() <= 5 and 3.0 < deg.mean() < 4.5          # ~5-point stencil with the diagonal
+    nx, ny, nz = 10, 8, 5
+    inner = [((y * nz + z) * nx + x) for z in range(1, nz - 1) for y in range(1, ny - 1) for x in range(1, nx - 1)]
+    assert set(deg[inner]) <= {3, 4, 5}
+    bn = np.diag(H).real[[(y * nz + 2) * nx + x for y in range(ny) for x in range(nx)]]
+    assert set(np.round(bn, 12)) == {2.0, -2.0}
+
+
+@pytest.mark.parametrize("geo", [True, False])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_trees_are_exact(geo, variant):
+    dev = W.gbng_device(12, 9, 5, seed=2)
+    st, cl = _tree(dev, 3, geo, variant)
+    _check_tree(dev, cl)
+
+
+def test_operation_count_grows_slower_than_rgf():
+    """RGF costs O(Nx^3 Nz^3 Ny), i.e. Nx^4 for Nx = Ny at fixed Nz; the paper reports the
+    HSC-extension at the LU factorisation's O(Nx^3). The model's slope between Nx = 32 and 192
+    (Nz = 5) stays between 2 and 3 under both orderings."""
+    Ns = [32, 64, 128, 192]
+    for geo in (True, False):
+        f = []
+        for N in Ns:
+            st, _ = _tree(W.gbng_device(N, N, 5, seed=0), 8, geo)
+            f.append(st.flops_gr + st.flops_gl)
+        slope = np.polyfit(np.log(Ns), np.log(f), 1)[0]
+        assert 1.8 < slope < 3.2, (geo, slope)
+
+
+@pytest.mark.parametrize("E", [-1.3, 0.4])
+def test_rgf_along_y_matches_the_dense_definition(E):
+    nx, ny, nz = 6, 5, 3
+    dev = W.gbng_device(nx, ny, nz, W=0.5, seed=3)
+    sr, sl = W.self_energies(dev, 1)
+    out = rgf.sweep(dev.to_scipy(), nx * nz, E, 1e-6, dev.contact_unknowns(), sr[0], sl[0],
+                    coupling_layers=(2,))
+    G, Gl = dense.solve(dev.to_scipy().toarray(), E, 1e-6, dev.contact_unknowns(), sr[0], sl[0])
+    assert np.abs(out["diag_gr"] - np.diag(G)).max() <= 1e-11 * np.abs(np.diag(G)).max()
+    assert np.abs(out["diag_gl"] - np.diag(Gl)).max() <= 1e-11 * np.abs(np.diag(Gl)).max()
