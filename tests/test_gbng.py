@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dense, rgf
 from paper_1702_05167_gb300 import hsc, workloads as W
-from test_abi_and_analysis import _check_tree, _tree
+from treecheck import _check_tree, _tree
 
 
 @pytest.fixture(scope="module", autouse=True)
