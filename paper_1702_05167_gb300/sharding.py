@@ -19,8 +19,9 @@ def shard(n_E: int, rank: int, world: int) -> np.ndarray:
 
 
 def interleaved_grid(E: np.ndarray, rank: int, world: int) -> np.ndarray:
-    """Weak-scaling grid of one rank: the common grid shifted by rank/world of a spacing."""
-    if world == 1:
+    """Weak-scaling grid of one rank: the common grid shifted by rank/world of a spacing (a grid of
+    one energy has no spacing and is returned as is)."""
+    if world == 1 or len(E) < 2:
         return E
     return E + (E[1] - E[0]) * rank / world
 
@@ -41,10 +42,15 @@ def partial_integral(E: np.ndarray, values: np.ndarray, owned: np.ndarray) -> np
 
 
 def allreduce_sum(x: np.ndarray, group=None) -> np.ndarray:
-    """Sum a host array over all ranks (torch.distributed; gloo on CPU, NCCL on GPU tensors)."""
+    """Sum a host array over all ranks (torch.distributed). NCCL reduces device tensors only, so
+    under that backend the array makes a round trip through the current CUDA device."""
     import torch
     import torch.distributed as dist
     t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
-    if dist.is_initialized() and dist.get_world_size() > 1:
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        if dist.get_backend(group) == "nccl":
+            d = t.to(torch.device("cuda", torch.cuda.current_device()))
+            dist.all_reduce(d, op=dist.ReduceOp.SUM, group=group)
+            return d.cpu().numpy()
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.numpy()

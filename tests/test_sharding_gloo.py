@@ -63,3 +63,9 @@ def test_interleaved_grids_are_disjoint():
     g = [sharding.interleaved_grid(E, r, 4) for r in range(4)]
     allE = np.concatenate(g)
     assert len(np.unique(np.round(allE, 12))) == 128
+
+
+def test_a_one_energy_grid_is_not_shifted():
+    E = np.array([0.25])
+    for r in range(3):
+        assert np.array_equal(sharding.interleaved_grid(E, r, 3), E)
