@@ -142,6 +142,25 @@ def _ptr(a):
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
+def _check_io(on_device, **bufs):
+    """Each buffer must hold float64 or complex128 values and live where io_on_device says: CUDA
+    tensors for device I/O, numpy arrays or CPU tensors for host I/O. The library cannot tell a
+    host pointer from a device one, and a wrong one would be dereferenced by a kernel."""
+    for name, a in bufs.items():
+        if a is None:
+            continue
+        if isinstance(a, np.ndarray):
+            if on_device:
+                raise ValueError(f"{name}: io_on_device needs CUDA tensors, got a numpy array")
+            if a.dtype not in (np.float64, np.complex128):
+                raise TypeError(f"{name}: float64 or complex128 expected, got {a.dtype}")
+        elif hasattr(a, "data_ptr"):
+            if bool(a.is_cuda) != bool(on_device):
+                raise ValueError(f"{name}: a {'CUDA' if on_device else 'host'} buffer is expected")
+            if str(a.dtype) not in ("torch.float64", "torch.complex128"):
+                raise TypeError(f"{name}: float64 or complex128 expected, got {a.dtype}")
+
+
 def _check(h, code):
     if code != HSC_OK:
         msg = load().hsc_last_error(h).decode(errors="replace")
@@ -185,6 +204,8 @@ def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, dia
     """Marshal buffers to hsc_solve. Buffers are numpy (host) or torch (device) arrays; complex128
     arrays are passed as interleaved doubles."""
     n_E = int(E.shape[0])
+    _check_io(io_on_device, E=E, sigma_r=sigma_r, sigma_less=sigma_less, diag_gr=diag_gr,
+              diag_gl=diag_gl, req_gr=req_gr, req_gl=req_gl)
     pairs = None
     n_req = 0
     if req_pairs is not None and len(req_pairs):
@@ -200,6 +221,8 @@ def hsc_solve(h, E, eta, sigma_r, sigma_less, precision, req_pairs, diag_gr, dia
 def hsc_scba(h, E, eta, sigma_r, sigma_less, d0, mix, tol, max_iter, precision, diag_gr, diag_gl,
              stream=None, io_on_device=False):
     """Marshal buffers to hsc_scba (as hsc_solve). Returns (solves made, last delta)."""
+    _check_io(io_on_device, E=E, sigma_r=sigma_r, sigma_less=sigma_less, diag_gr=diag_gr,
+              diag_gl=diag_gl)
     it = ctypes.c_int32()
     dl = ctypes.c_double()
     s = None if stream is None else ctypes.c_void_p(int(stream))
@@ -214,6 +237,8 @@ def hsc_scba(h, E, eta, sigma_r, sigma_less, d0, mix, tol, max_iter, precision, 
 def hsc_solve_dense(h, E, eta, sigma_r, sigma_less, dense_r, dense_less, precision, req_pairs, diag_gr,
                     diag_gl, req_gr, req_gl, stream=None, io_on_device=False):
     """Marshal buffers to hsc_solve_dense (as hsc_solve, plus the dense contact blocks)."""
+    _check_io(io_on_device, E=E, sigma_r=sigma_r, sigma_less=sigma_less, dense_r=dense_r,
+              dense_less=dense_less, diag_gr=diag_gr, diag_gl=diag_gl, req_gr=req_gr, req_gl=req_gl)
     pairs = None
     n_req = 0
     if req_pairs is not None and len(req_pairs):
@@ -246,6 +271,8 @@ def hsc_solve_batch(items, eta, precision, stream=None, use_graph=True):
     arr = (hsc_batch_item * len(items))()
     keep = []
     for k, it in enumerate(items):
+        _check_io(True, **{f"items[{k}].{x}": it.get(x) for x in ("E", "sigma_r", "sigma_less", "diag_gr",
+                                                                  "diag_gl", "req_gr", "req_gl")})
         pairs = it.get("pairs")
         if pairs is not None and len(pairs):
             pairs = np.ascontiguousarray(pairs, dtype=np.int32)

@@ -303,3 +303,26 @@ def test_options_round_trip_and_reject_bad_values():
     with pytest.raises(hsc.HSCError):
         hsc.hsc_solve_batch([], 0.05, hsc.HSC_FP64)
     hsc.hsc_destroy(h)
+
+
+def test_binding_rejects_buffers_of_the_wrong_kind_before_the_call():
+    """A host array given for device I/O (or a float32 array) would be read as something else by the
+    library; the binding refuses it before any C call."""
+    import torch
+    dev = W.cubic_device((3, 3, 3), seed=0)
+    h = _handle(dev)
+    hsc.hsc_analyze(h, 2)
+    sr, sl = W.self_energies(dev, 1)
+    out = np.zeros((1, dev.n), np.complex128)
+    E = np.array([0.1])
+    with pytest.raises(ValueError):
+        hsc.hsc_solve(h, E, 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(), None, None, io_on_device=True)
+    with pytest.raises(TypeError):
+        hsc.hsc_solve(h, E.astype(np.float32), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(), None, None)
+    with pytest.raises(ValueError):
+        hsc.hsc_scba(h, torch.from_numpy(E), 1e-6, sr, sl, 0.1, 0.5, 1e-8, 3, hsc.HSC_FP64, out, out.copy(),
+                     io_on_device=True)
+    with pytest.raises(TypeError):
+        hsc.hsc_solve(h, torch.from_numpy(E).float(), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(),
+                      None, None)
+    hsc.hsc_destroy(h)
