@@ -192,7 +192,8 @@ typedef enum {
   HSC_OPT_ORDERING = 9        /* 1: the next hsc_analyze uses breadth-first level-set bisection */
                               /* of the site graph even when grid_dims were given (its level     */
                               /* sets from a corner are diagonal planes: on a 32^3 cube the     */
-                              /* model counts 260 instead of 369 GFLOP per energy, on 24^3 more)*/
+                              /* model counts 260 instead of 369 GFLOP per energy, on 24^3 more;*/
+                              /* at eta = 1e-6 they lose more digits than axis planes)          */
                               /* 0 (default): geometric dissection when grid_dims were given    */
 } hsc_option;
 
