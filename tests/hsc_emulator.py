@@ -17,17 +17,20 @@ def tree(h, n_clusters):
     return out
 
 
-def selected(A, L, clusters):
+def selected(A, L, clusters, stats=None):
     """Upward elimination in postorder, then downward selected inversion root first.
 
     A: dense complex-symmetric system matrix; L: dense anti-Hermitian Sigma^<; clusters: list of
     (own unknowns in local order, update set U_i) in postorder. Returns dense G, P holding the
-    selected blocks of G^r and G^< (zeros elsewhere).
+    selected blocks of G^r and G^< (zeros elsewhere). If stats is a dict, stats["growth"] receives
+    the largest |Re| + |Im| of any D_i^{-1} entry (what hsc_growth records).
     """
     Aw, Lw = A.astype(np.complex128).copy(), L.astype(np.complex128).copy()
     fac = []
     for I, U in clusters:
         Dinv = np.linalg.inv(Aw[np.ix_(I, I)])
+        if stats is not None:
+            stats["growth"] = max(stats.get("growth", 0.0), float((np.abs(Dinv.real) + np.abs(Dinv.imag)).max()))
         X = Dinv @ Aw[np.ix_(I, U)]
         Lii, LiU = Lw[np.ix_(I, I)].copy(), Lw[np.ix_(I, U)].copy()
         if len(U):
