@@ -23,14 +23,17 @@ def selected(A, L, clusters, stats=None):
     A: dense complex-symmetric system matrix; L: dense anti-Hermitian Sigma^<; clusters: list of
     (own unknowns in local order, update set U_i) in postorder. Returns dense G, P holding the
     selected blocks of G^r and G^< (zeros elsewhere). If stats is a dict, stats["growth"] receives
-    the largest |Re| + |Im| of any D_i^{-1} entry (what hsc_growth records).
+    the largest |Re| + |Im| of any D_i^{-1} entry (what hsc_growth records) and
+    stats["cluster_growth"] that value per cluster.
     """
     Aw, Lw = A.astype(np.complex128).copy(), L.astype(np.complex128).copy()
     fac = []
     for I, U in clusters:
         Dinv = np.linalg.inv(Aw[np.ix_(I, I)])
         if stats is not None:
-            stats["growth"] = max(stats.get("growth", 0.0), float((np.abs(Dinv.real) + np.abs(Dinv.imag)).max()))
+            g = float((np.abs(Dinv.real) + np.abs(Dinv.imag)).max())
+            stats["growth"] = max(stats.get("growth", 0.0), g)
+            stats.setdefault("cluster_growth", []).append(g)
         X = Dinv @ Aw[np.ix_(I, U)]
         Lii, LiU = Lw[np.ix_(I, I)].copy(), Lw[np.ix_(I, U)].copy()
         if len(U):
@@ -54,3 +57,31 @@ def selected(A, L, clusters, stats=None):
         G[np.ix_(I, I)], G[np.ix_(I, U)], G[np.ix_(U, I)] = Gii, GiU, GiU.T
         P[np.ix_(I, I)], P[np.ix_(I, U)], P[np.ix_(U, I)] = Pii, PiU, -PiU.conj().T
     return G, P
+
+
+def update_sets(owns, H):
+    """Exact update sets for clusters given as own-unknown lists in elimination order (children
+    before parents), by symbolic elimination: a cluster absorbs the pending boundary of every earlier
+    cluster that reaches it. For trees the analysis does not build (merged clusters)."""
+    n = H.shape[0]
+    owner = np.empty(n, int)
+    for i, o in enumerate(owns):
+        owner[o] = i
+    coo = H.tocoo()
+    adj = [set() for _ in range(n)]
+    for a, b in zip(coo.row, coo.col):
+        if a != b:
+            adj[a].add(b)
+    reach, taken = [], [False] * len(owns)
+    for i, own in enumerate(owns):
+        dom = set(own.tolist())
+        ext = set()
+        for u in own:
+            ext |= adj[u]
+        for j in range(i):
+            if not taken[j] and reach[j] & dom:
+                taken[j] = True
+                ext |= reach[j]
+        reach.append({u for u in ext - dom if owner[u] > i})
+    return [(np.asarray(own, np.int64), np.array(sorted(r, key=lambda u: (owner[u], u)), dtype=np.int64))
+            for own, r in zip(owns, reach)]
