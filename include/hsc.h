@@ -86,6 +86,17 @@ int hsc_create(hsc_t* out, int64_t n, int32_t orb,
  *   at leaf_max^3 sites. stats may be NULL. Errors: HSC_ERR_ARG, HSC_ERR_OOM. */
 int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats);
 
+/* hsc_set_merge -- merge clusters into their parents at the next hsc_analyze.
+ *   clusters[n]: ids of the tree that hsc_analyze builds without a merge list (n = 0 clears it). Each
+ *   listed cluster's own unknowns join its parent's and its children become the parent's; where a
+ *   cluster would get more than two children, pass-through clusters with no own unknowns pair them
+ *   up (their fronts carry the children's updates on unchanged). Delayed pivoting at cluster
+ *   granularity: a cluster whose block has a level close to E is eliminated together with its
+ *   separator. The call discards the tree and device state: hsc_analyze must run again.
+ *   The analysis is tested on the CPU; solves on merged trees have not been run on a GB300 yet.
+ *   Errors: HSC_ERR_ARG (negative id; at hsc_analyze: id out of range or the root). */
+int hsc_set_merge(hsc_t h, int32_t n, const int32_t* clusters);
+
 /* hsc_set_contact_dense -- mark contact `contact` as DENSE (dense = 1) or diagonal (0, the default).
  *   Section 3.1.2 models open boundaries with a dense self-energy block on the contact layer, which
  *   couples every pair of the contact's unknowns. The next hsc_analyze then keeps each dense

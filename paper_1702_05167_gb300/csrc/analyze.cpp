@@ -146,7 +146,8 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
   const int64_t ns = in.n / orb;
   P.n_sites = ns;
 
-  Builder B(in, ns, leaf_max, P.cl);
+  std::vector<Cluster> first;   // the tree before merges (when a merge list is given)
+  Builder B(in, ns, leaf_max, in.n_merge > 0 ? first : P.cl);
   // site graph from the unknown-level CSR
   B.adj.assign(ns, {});
   for (int64_t u = 0; u < in.n; ++u) {
@@ -218,6 +219,50 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
   for (int c : dense_c) {
     std::vector<int> sites(in.contact_sites + in.contact_ptr[c], in.contact_sites + in.contact_ptr[c + 1]);
     top = B.make(std::move(sites), top, -1);
+  }
+  if (in.n_merge > 0) {
+    // Merge the listed clusters' own sites into their parents (children of a merged cluster become
+    // its parent's). A cluster left with more than two children gets pass-through clusters of no
+    // own unknowns: each takes two subtrees and hands their updates on unchanged.
+    const int n0 = (int)first.size();
+    if (n0 == 0) return "empty tree";
+    std::vector<char> merged(n0, 0);
+    for (int k = 0; k < in.n_merge; ++k) {
+      const int c = in.merge[k];
+      if (c < 0 || c >= n0) return "merge list: cluster id out of range";
+      if (first[c].parent < 0) return "merge list: the root has no parent";
+      merged[c] = 1;
+    }
+    std::vector<Cluster> out;
+    Builder M(in, ns, leaf_max, out);
+    auto pair_up = [&](std::vector<int>& kids) {
+      while (kids.size() > 2) {
+        const int a = kids.back(); kids.pop_back();
+        const int b = kids.back(); kids.pop_back();
+        kids.push_back(M.make(std::vector<int>(), b, a));
+      }
+    };
+    // own sites and new child ids of cluster i with its merged children folded in
+    std::function<void(int, std::vector<int>&, std::vector<int>&)> gather =
+        [&](int i, std::vector<int>& sites, std::vector<int>& kids) {
+          sites.insert(sites.end(), first[i].sites.begin(), first[i].sites.end());
+          for (int k = 0; k < first[i].nchild; ++k) {
+            const int c = first[i].child[k];
+            if (merged[c]) {
+              gather(c, sites, kids);
+            } else {
+              std::vector<int> cs, ck;
+              gather(c, cs, ck);
+              pair_up(ck);
+              kids.push_back(M.make(std::move(cs), ck.size() > 0 ? ck[0] : -1, ck.size() > 1 ? ck[1] : -1));
+            }
+          }
+        };
+    std::vector<int> rs, rk;
+    gather(n0 - 1, rs, rk);
+    pair_up(rk);
+    M.make(std::move(rs), rk.size() > 0 ? rk[0] : -1, rk.size() > 1 ? rk[1] : -1);
+    P.cl = std::move(out);
   }
   auto& cl = P.cl;
   const int nc = (int)cl.size();

@@ -118,6 +118,8 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   if (h->opt_ordering == 1) in.dims[0] = in.dims[1] = in.dims[2] = 0;   // graph bisection
   in.variant = h->nd_variant;
   in.contact_dense = h->contact_dense.empty() ? nullptr : h->contact_dense.data();
+  in.merge = h->merge.empty() ? nullptr : h->merge.data();
+  in.n_merge = (int)h->merge.size();
   hsc_drop_alt(h);   // the twin follows the leaf size of this analysis
   std::string e;
   try {
@@ -231,6 +233,20 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_ORDERING: *value = h->opt_ordering; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
+  return HSC_OK;
+}
+
+extern "C" int hsc_set_merge(hsc_t h, int32_t n, const int32_t* clusters) {
+  if (!h) return hsc_fail(nullptr, HSC_ERR_ARG, "handle is NULL");
+  if (h->is_alt || n < 0 || (n > 0 && !clusters)) return hsc_fail(h, HSC_ERR_ARG, "bad merge list");
+  for (int32_t k = 0; k < n; ++k)
+    if (clusters[k] < 0) return hsc_fail(h, HSC_ERR_ARG, "negative cluster id in the merge list");
+  h->merge.assign(clusters, clusters + n);
+  h->analyzed = false;   // the tree changes: analyse again
+  hsc::device_state_free(h->dev);
+  h->dev = nullptr;
+  hsc_drop_alt(h);
+  h->err.clear();
   return HSC_OK;
 }
 

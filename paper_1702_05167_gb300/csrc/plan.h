@@ -92,6 +92,9 @@ struct Input {
   int dims[3] = {0, 0, 0};   // all zero: general graph bisection
   int variant = 0;           // 1..4: alternate separator trees (cuts below the root moved +1, -1, +2, -2)
   const char* contact_dense = nullptr;   // per contact (nullable): 1 = one cluster on top of the tree
+  // clusters (ids of the tree built without merges) whose own unknowns join their parent's
+  const int32_t* merge = nullptr;
+  int n_merge = 0;
 };
 
 // Builds the plan. Returns an empty string on success, else an error message.

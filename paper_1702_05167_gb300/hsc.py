@@ -19,6 +19,7 @@ STATUS = {0: "HSC_OK", 1: "HSC_ERR_ARG", 2: "HSC_ERR_NOT_SYMMETRIC", 3: "HSC_ERR
 
 EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
            "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_set_contact_dense", "hsc_solve_dense",
+           "hsc_set_merge",
            "hsc_profile",
            "hsc_profile_read", "hsc_growth",
            "hsc_residual",
@@ -95,6 +96,7 @@ def load():
                            ctypes.POINTER(hsc_tune_result)]
     L.hsc_set_option.argtypes = [vp, i32, i32]
     L.hsc_set_contact_dense.argtypes = [vp, i32, i32]
+    L.hsc_set_merge.argtypes = [vp, i32, vp]
     L.hsc_solve_dense.argtypes = [vp, i64, vp, dp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, i32]
     L.hsc_get_option.argtypes = [vp, i32, ctypes.POINTER(i32)]
     L.hsc_observables.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp]
@@ -119,7 +121,7 @@ def load():
     for name in ("hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_batch",
                  "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_profile",
                  "hsc_profile_read", "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba",
-                 "hsc_set_contact_dense", "hsc_solve_dense", "hsc_destroy",
+                 "hsc_set_contact_dense", "hsc_solve_dense", "hsc_set_merge", "hsc_destroy",
                  "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
                  "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"):
         getattr(L, name).restype = ctypes.c_int
@@ -253,6 +255,11 @@ def hsc_solve_dense(h, E, eta, sigma_r, sigma_less, dense_r, dense_less, precisi
 
 def hsc_set_option(h, option, value):
     _check(h, load().hsc_set_option(h, int(option), int(value)))
+
+
+def hsc_set_merge(h, clusters):
+    arr = np.ascontiguousarray(clusters, dtype=np.int32)
+    _check(h, load().hsc_set_merge(h, len(arr), _ptr(arr) if len(arr) else None))
 
 
 def hsc_set_contact_dense(h, contact, dense=True):

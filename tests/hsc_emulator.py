@@ -31,7 +31,7 @@ def selected(A, L, clusters, stats=None):
     for I, U in clusters:
         Dinv = np.linalg.inv(Aw[np.ix_(I, I)])
         if stats is not None:
-            g = float((np.abs(Dinv.real) + np.abs(Dinv.imag)).max())
+            g = float((np.abs(Dinv.real) + np.abs(Dinv.imag)).max()) if Dinv.size else 0.0
             stats["growth"] = max(stats.get("growth", 0.0), g)
             stats.setdefault("cluster_growth", []).append(g)
         X = Dinv @ Aw[np.ix_(I, U)]
