@@ -200,12 +200,16 @@ typedef enum {
                               /* hsc_solve_batch does not re-solve.                             */
   HSC_OPT_TREE_VARIANT = 8,   /* 1..4: the next hsc_analyze builds that alternate separator     */
                               /* tree itself (0, default: the plain tree)                       */
-  HSC_OPT_ORDERING = 9        /* 1: the next hsc_analyze uses breadth-first level-set bisection */
+  HSC_OPT_ORDERING = 9,       /* 1: the next hsc_analyze uses breadth-first level-set bisection */
                               /* of the site graph even when grid_dims were given (its level     */
                               /* sets from a corner are diagonal planes: on a 32^3 cube the     */
                               /* model counts 260 instead of 369 GFLOP per energy, on 24^3 more;*/
                               /* at eta = 1e-6 they lose more digits than axis planes)          */
                               /* 0 (default): geometric dissection when grid_dims were given    */
+  HSC_OPT_MAX_CLUSTER = 10    /* > 0: the next hsc_analyze splits every cluster of more sites   */
+                              /* into a chain of pieces of at most that many sites, each the    */
+                              /* parent of the previous (Section 3.4's degenerate sub-trees for */
+                              /* dense molecular blocks); dense contacts stay whole; 0 = off    */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);

@@ -147,7 +147,8 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
   P.n_sites = ns;
 
   std::vector<Cluster> first;   // the tree before merges (when a merge list is given)
-  Builder B(in, ns, leaf_max, in.n_merge > 0 ? first : P.cl);
+  const bool rebuild = in.n_merge > 0 || in.max_cluster > 0;
+  Builder B(in, ns, leaf_max, rebuild ? first : P.cl);
   // site graph from the unknown-level CSR
   B.adj.assign(ns, {});
   for (int64_t u = 0; u < in.n; ++u) {
@@ -220,10 +221,11 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
     std::vector<int> sites(in.contact_sites + in.contact_ptr[c], in.contact_sites + in.contact_ptr[c + 1]);
     top = B.make(std::move(sites), top, -1);
   }
-  if (in.n_merge > 0) {
+  if (rebuild) {
     // Merge the listed clusters' own sites into their parents (children of a merged cluster become
     // its parent's). A cluster left with more than two children gets pass-through clusters of no
-    // own unknowns: each takes two subtrees and hands their updates on unchanged.
+    // own unknowns: each takes two subtrees and hands their updates on unchanged. Then a cluster of
+    // more than max_cluster sites becomes a chain of pieces (each parent of the previous one).
     const int n0 = (int)first.size();
     if (n0 == 0) return "empty tree";
     std::vector<char> merged(n0, 0);
@@ -235,6 +237,17 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
     }
     std::vector<Cluster> out;
     Builder M(in, ns, leaf_max, out);
+    auto make_split = [&](std::vector<int>&& sites, int c0, int c1) {
+      const size_t K = (size_t)in.max_cluster;
+      if (K == 0 || sites.size() <= K || (!sites.empty() && in_dense[sites[0]])) return M.make(std::move(sites), c0, c1);
+      std::sort(sites.begin(), sites.end());
+      int cur = -1;
+      for (size_t a = 0; a < sites.size(); a += K) {
+        std::vector<int> piece(sites.begin() + a, sites.begin() + std::min(sites.size(), a + K));
+        cur = a == 0 ? M.make(std::move(piece), c0, c1) : M.make(std::move(piece), cur, -1);
+      }
+      return cur;
+    };
     auto pair_up = [&](std::vector<int>& kids) {
       while (kids.size() > 2) {
         const int a = kids.back(); kids.pop_back();
@@ -254,14 +267,14 @@ std::string analyze(const Input& in, int leaf_max, Plan& P) {
               std::vector<int> cs, ck;
               gather(c, cs, ck);
               pair_up(ck);
-              kids.push_back(M.make(std::move(cs), ck.size() > 0 ? ck[0] : -1, ck.size() > 1 ? ck[1] : -1));
+              kids.push_back(make_split(std::move(cs), ck.size() > 0 ? ck[0] : -1, ck.size() > 1 ? ck[1] : -1));
             }
           }
         };
     std::vector<int> rs, rk;
     gather(n0 - 1, rs, rk);
     pair_up(rk);
-    M.make(std::move(rs), rk.size() > 0 ? rk[0] : -1, rk.size() > 1 ? rk[1] : -1);
+    make_split(std::move(rs), rk.size() > 0 ? rk[0] : -1, rk.size() > 1 ? rk[1] : -1);
     P.cl = std::move(out);
   }
   auto& cl = P.cl;

@@ -119,6 +119,7 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   in.variant = h->nd_variant;
   in.contact_dense = h->contact_dense.empty() ? nullptr : h->contact_dense.data();
   in.merge = h->merge.empty() ? nullptr : h->merge.data();
+  in.max_cluster = h->opt_max_cluster;
   in.n_merge = (int)h->merge.size();
   hsc_drop_alt(h);   // the twin follows the leaf size of this analysis
   std::string e;
@@ -210,6 +211,10 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       if (value < 0 || value > 1) return hsc_fail(h, HSC_ERR_ARG, "ordering must be 0 or 1");
       h->opt_ordering = value;
       break;
+    case HSC_OPT_MAX_CLUSTER:
+      if (value < 0) return hsc_fail(h, HSC_ERR_ARG, "max cluster size must be >= 0");
+      h->opt_max_cluster = value;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
@@ -231,6 +236,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_RESOLVE_DIGITS: *value = h->opt_resolve; break;
     case HSC_OPT_TREE_VARIANT: *value = h->nd_variant; break;
     case HSC_OPT_ORDERING: *value = h->opt_ordering; break;
+    case HSC_OPT_MAX_CLUSTER: *value = h->opt_max_cluster; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
   return HSC_OK;
@@ -299,6 +305,7 @@ hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
   a->opt_4m = h->opt_4m;
   a->opt_fp64_engine = h->opt_fp64_engine;
   a->opt_ordering = h->opt_ordering;
+  a->opt_max_cluster = h->opt_max_cluster;
   a->nd_variant = v;
   a->is_alt = true;
   if (hsc_analyze(a, h->leaf_max, nullptr) != HSC_OK) {

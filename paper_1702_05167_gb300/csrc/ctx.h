@@ -37,6 +37,7 @@ struct hsc_ctx {
   int opt_resolve = 4;        // d: re-solve energies whose residual exceeds 10^-d (0: off)
   int opt_ordering = 0;       // 1: graph bisection even when grid_dims are given (next analyze)
   std::vector<int32_t> merge; // clusters merged into their parents by the next analyze
+  int opt_max_cluster = 0;    // > 0: split larger clusters into chains (next analyze)
   int leaf_max = 0;           // last hsc_analyze leaf size
   // alternate separator trees 1..4 (cuts below the root shifted), built on first need by hsc_solve
   int nd_variant = 0;

@@ -95,6 +95,9 @@ struct Input {
   // clusters (ids of the tree built without merges) whose own unknowns join their parent's
   const int32_t* merge = nullptr;
   int n_merge = 0;
+  // > 0: a cluster of more sites is split into a chain of pieces of at most this many sites (the
+  // degenerate sub-trees of Section 3.4); dense contacts stay whole
+  int max_cluster = 0;
 };
 
 // Builds the plan. Returns an empty string on success, else an error message.
