@@ -326,3 +326,14 @@ def test_binding_rejects_buffers_of_the_wrong_kind_before_the_call():
         hsc.hsc_solve(h, torch.from_numpy(E).float(), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(),
                       None, None)
     hsc.hsc_destroy(h)
+
+
+def test_metric_workload_tree_is_unchanged():
+    """The 32^3 workload's tree (leaves <= 8) and its model: 127 clusters over 7 levels, largest
+    front 1024 x 2048, 179.5 + 189.6 GFLOP per energy (the figures the measurements use)."""
+    dev = W.cubic_device((32, 32, 32), seed=0)
+    h = _handle(dev)
+    st = hsc.hsc_analyze(h, 8)
+    hsc.hsc_destroy(h)
+    assert (st.n_clusters, st.n_heights, st.n_depths, st.max_n, st.max_m) == (127, 7, 7, 1024, 1024)
+    assert abs(st.flops_gr - 179528180960.0) <= 1.0 and abs(st.flops_gl - 189624310312.0) <= 1.0
