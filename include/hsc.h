@@ -200,16 +200,34 @@ typedef enum {
                               /* hsc_solve_batch does not re-solve.                             */
   HSC_OPT_TREE_VARIANT = 8,   /* 1..4: the next hsc_analyze builds that alternate separator     */
                               /* tree itself (0, default: the plain tree)                       */
-  HSC_OPT_ORDERING = 9,       /* 1: the next hsc_analyze uses breadth-first level-set bisection */
-                              /* of the site graph even when grid_dims were given (its level     */
-                              /* sets from a corner are diagonal planes: on a 32^3 cube the     */
-                              /* model counts 260 instead of 369 GFLOP per energy, on 24^3 more;*/
-                              /* at eta = 1e-6 they lose more digits than axis planes)          */
-                              /* 0 (default): geometric dissection when grid_dims were given    */
-  HSC_OPT_MAX_CLUSTER = 10    /* > 0: the next hsc_analyze splits every cluster of more sites   */
+  HSC_OPT_ORDERING = 9,       /* tree of the next hsc_analyze when grid_dims were given:        */
+                              /* 0 (default): geometric dissection; when every contact site    */
+                              /* lies on the end planes x = 0 and x = Nx-1 (both used), in its  */
+                              /* contact-connected form: x is cut once, at the root, and every  */
+                              /* deeper cut is a y or z plane (leaves: leaf_max x leaf_max      */
+                              /* cross-sections spanning half the device), so every cluster     */
+                              /* below the root keeps a share of a contact face. Clusters far   */
+                              /* from both contacts carry only eta in their blocks, and at small*/
+                              /* eta one with a level within delta of E costs the downward pass */
+                              /* ~1/delta^2 in rounding (on the 32^3 cube at eta = 1e-6 the    */
+                              /* plain tree loses 2 to 17 digits, this one 0 to 2; it costs     */
+                              /* 855 instead of 369 model GFLOP per energy with leaf_max 8).    */
+                              /* 1: breadth-first level-set bisection of the site graph (level  */
+                              /* sets from a corner are diagonal planes: 260 GFLOP on 32^3; they*/
+                              /* lose more digits at small eta than axis planes)                */
+                              /* 2: plain geometric dissection (the longest extent is cut at    */
+                              /* every level: 8^3 leaves and 369 GFLOP on 32^3 with leaf_max 8) */
+  HSC_OPT_MAX_CLUSTER = 10,   /* > 0: the next hsc_analyze splits every cluster of more sites   */
                               /* into a chain of pieces of at most that many sites, each the    */
                               /* parent of the previous (Section 3.4's degenerate sub-trees for */
                               /* dense molecular blocks); dense contacts stay whole; 0 = off    */
+  HSC_OPT_TREE_FORM = 11      /* read only: the tree of the last hsc_analyze: 0 plain geometric,*/
+                              /* 1 contact-connected geometric, 2 graph bisection (-1 before    */
+                              /* any analysis). With HSC_OPT_ORDERING = 0 the contact-connected */
+                              /* form is taken only while its model cost stays within 3x the    */
+                              /* plain geometric tree's or below 1 GFLOP per energy (an         */
+                              /* elongated device, e.g. a 64 x 12 x 12 wire, keeps the plain    */
+                              /* form)                                                          */
 } hsc_option;
 
 int hsc_set_option(hsc_t h, int32_t option, int32_t value);
@@ -298,6 +316,18 @@ int hsc_residual(hsc_t h, int64_t n_E, double* out);
  *   Errors: HSC_ERR_ARG, HSC_ERR_STATE (no such solve), HSC_ERR_CUDA. */
 int hsc_growth(hsc_t h, int64_t n_E, double* out);
 
+/* hsc_cluster_growth -- per-cluster conditioning record of the last solve on this handle:
+ *   out[k][c] = ||D_c^{-1}||_F (Frobenius norm, 1/eV) of cluster c's block of Algorithm 1 (Eq. 3) at
+ *   energy k, for the clusters of this handle's own tree (postorder ids as hsc_cluster; 0 for a
+ *   cluster with no own unknowns). It lies between 1/sigma_min(D_c) and sqrt(n_c)/sigma_min(D_c),
+ *   so a level of the block within delta of E reads as ~1/delta. At small eta an interior block with
+ *   such a level makes the downward step G_cc = D_c^{-1} + X_c G_UU X_c^T cancel terms of size
+ *   ~1/delta^2, amplifying the rounding error its ancestors' blocks carry by about that factor.
+ *   Energies that a re-solve moved to another tree keep the record of this tree.
+ *   out: host array of n_E x n_clusters doubles, n_E <= the last solve's n_E. Synchronises the
+ *   device. Errors: HSC_ERR_ARG, HSC_ERR_STATE (no such solve), HSC_ERR_CUDA. */
+int hsc_cluster_growth(hsc_t h, int64_t n_E, double* out);
+
 /* hsc_profile -- reset the kernel statistics; enable = 1 additionally brackets every kernel launch
  *   of subsequent hsc_solve calls with CUDA events on the solve's stream (device-side timing;
  *   a small host overhead per launch), enable = 0 stops the timing. No GPU work. */
@@ -361,11 +391,14 @@ int hsc_device_fp64_peaks(double* dmma_gflops, double* dfma_gflops);
  *   Ainv  device, same layout, receives the inverses (may equal A: in place)
  *   cuda_stream  stream to run on (NULL: legacy default stream); the call synchronises it.
  *   Limits: n <= 1024, batch <= 256, n * batch <= 8192. Scratch lives in one fixed 4.3 MiB device
- *   array per device (held until process exit); no cudaMalloc/cudaFree is called. The first call on
- *   a device looks up that array's address (cudaGetSymbolAddress) and should come before any stream
- *   capture. Calls whose work overlaps on the GPU race on the shared array: serialise them.
- *   Errors: HSC_ERR_ARG (sizes beyond the limits, NULL pointers), HSC_ERR_SINGULAR (zero pivot),
- *   HSC_ERR_CUDA. */
+ *   array per device (held until process exit); no cudaMalloc/cudaFree is called. The array exists
+ *   on a device from the first call there (the library's CUDA modules load lazily): that call loads
+ *   the module and looks up the array's address (cudaGetSymbolAddress). A call with batch = 0 (A and
+ *   Ainv may be NULL) does only this set-up; make it on each device before the memory pool reserves
+ *   the free device memory and before any stream capture. The cached address does not survive
+ *   cudaDeviceReset. Calls whose work overlaps on the GPU race on the shared array: serialise them.
+ *   Errors: HSC_ERR_ARG (sizes beyond the limits, NULL pointers), HSC_ERR_SINGULAR (zero pivot;
+ *   the outputs are then undefined), HSC_ERR_CUDA. */
 int hsc_block_inverse_noalloc(int32_t n, int32_t batch, const hsc_c128* A, hsc_c128* Ainv,
                               void* cuda_stream);
 

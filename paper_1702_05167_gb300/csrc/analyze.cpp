@@ -37,6 +37,12 @@ struct Builder {
   // alternate trees keep the root plane and move every deeper cut by +1, -1, +2 or -2 planes
   // (in.variant = 1..4) where both halves stay non-empty, so their boxes (and isolated spectra)
   // differ.
+  // Contact-connected form (in.contact_connected, for contacts on the end planes x = 0 and
+  // x = Nx-1): the root cuts x; below it only the longer of y and z is cut, and a box is a leaf once
+  // its y and z extents are <= leaf. Every cluster below the root then holds contact sites or has
+  // children that do, so no cluster block of Algorithm 1 lacks the contacts' broadening; a box far
+  // from both contacts would carry only eta, and a level of it within delta of E costs the
+  // downward step of Eq. 4 a factor ~1/delta^2 of the rounding error.
   int box(int lo[3], int hi[3], int depth = 0) {
     int ext[3];
     for (int d = 0; d < 3; ++d) {
@@ -51,10 +57,19 @@ struct Builder {
           for (int z = a[2]; z <= b[2]; ++z) s.push_back((x * Ny + y) * Nz + z);
       return s;
     };
-    if (ext[0] <= leaf && ext[1] <= leaf && ext[2] <= leaf) return make(sites_in(lo, hi), -1, -1);
+    const bool cc = in.contact_connected != 0;
+    const bool xcut = cc && depth == 0 && ext[0] >= 3;   // the one cut across the transport axis
+    if (!xcut && (cc || ext[0] <= leaf) && ext[1] <= leaf && ext[2] <= leaf)
+      return make(sites_in(lo, hi), -1, -1);
     int d = 0;
-    for (int k = 1; k < 3; ++k)
-      if (ext[k] > ext[d]) d = k;
+    if (xcut) {
+      d = 0;
+    } else if (cc) {
+      d = ext[2] > ext[1] ? 2 : 1;
+    } else {
+      for (int k = 1; k < 3; ++k)
+        if (ext[k] > ext[d]) d = k;
+    }
     int mid = (lo[d] + hi[d]) / 2;
     if (depth > 0 && in.variant > 0) {
       static const int kShift[5] = {0, 1, -1, 2, -2};

@@ -116,6 +116,19 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   in.contact_sites = h->contact_sites.data();
   std::memcpy(in.dims, h->dims, sizeof(in.dims));
   if (h->opt_ordering == 1) in.dims[0] = in.dims[1] = in.dims[2] = 0;   // graph bisection
+  if (h->opt_ordering == 0 && in.dims[0] > 0) {
+    // contact-connected dissection when every contact site lies on x = 0 or x = Nx-1 and both end
+    // planes hold some (a two-terminal device along x); otherwise the plain geometric form
+    const int64_t plane = (int64_t)in.dims[1] * in.dims[2];
+    bool lo = false, hi = false, ends = plane > 0;
+    for (int64_t k = 0; ends && k < (int64_t)h->contact_sites.size(); ++k) {
+      const int64_t x = h->contact_sites[k] / plane;
+      lo |= x == 0;
+      hi |= x == in.dims[0] - 1;
+      ends = x == 0 || x == in.dims[0] - 1;
+    }
+    in.contact_connected = ends && lo && hi && in.dims[0] >= 3 ? 1 : 0;
+  }
   in.variant = h->nd_variant;
   in.contact_dense = h->contact_dense.empty() ? nullptr : h->contact_dense.data();
   in.merge = h->merge.empty() ? nullptr : h->merge.data();
@@ -125,10 +138,25 @@ extern "C" int hsc_analyze(hsc_t h, int32_t leaf_max, hsc_tree_stats* stats) {
   std::string e;
   try {
     e = hsc::analyze(in, leaf_max, h->plan);
+    if (e.empty() && in.contact_connected) {
+      // an elongated device makes the half-device boxes costly: keep the contact-connected tree
+      // only while its model cost stays within 3x the plain geometric tree's (or below 1 GFLOP per
+      // energy, where the cost does not matter)
+      hsc::Input plain = in;
+      plain.contact_connected = 0;
+      hsc::Plan alt;
+      e = hsc::analyze(plain, leaf_max, alt);
+      const double fc = h->plan.flops_gr + h->plan.flops_gl, fp = alt.flops_gr + alt.flops_gl;
+      if (e.empty() && fc > 3.0 * fp && fc > 1e9) {
+        h->plan = std::move(alt);
+        in.contact_connected = 0;
+      }
+    }
   } catch (const std::bad_alloc&) {
     return hsc_fail(h, HSC_ERR_OOM, "out of host memory in analyze");
   }
   if (!e.empty()) return hsc_fail(h, HSC_ERR_ARG, e);
+  h->tree_form = in.dims[0] <= 0 ? 2 : (in.contact_connected ? 1 : 0);
   const hsc::Plan& P = h->plan;
   hsc_tree_stats s{};
   s.n_clusters = (int32_t)P.cl.size();
@@ -208,7 +236,7 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       h->nd_variant = value;
       break;
     case HSC_OPT_ORDERING:
-      if (value < 0 || value > 1) return hsc_fail(h, HSC_ERR_ARG, "ordering must be 0 or 1");
+      if (value < 0 || value > 2) return hsc_fail(h, HSC_ERR_ARG, "ordering must be 0, 1 or 2");
       h->opt_ordering = value;
       break;
     case HSC_OPT_MAX_CLUSTER:
@@ -236,6 +264,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_RESOLVE_DIGITS: *value = h->opt_resolve; break;
     case HSC_OPT_TREE_VARIANT: *value = h->nd_variant; break;
     case HSC_OPT_ORDERING: *value = h->opt_ordering; break;
+    case HSC_OPT_TREE_FORM: *value = h->analyzed ? h->tree_form : -1; break;
     case HSC_OPT_MAX_CLUSTER: *value = h->opt_max_cluster; break;
     default: return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }

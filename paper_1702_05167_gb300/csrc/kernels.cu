@@ -342,9 +342,13 @@ __global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32
 }
 
 // undo the row interchanges on the columns of the in-place inverse: A^{-1} = Y P
-// Also records the growth of the energy: the largest |Re| + |Im| of any entry of D_i^{-1}.
+// Also records the growth of the energy: the largest |Re| + |Im| of any entry of D_i^{-1}, and,
+// per (energy, block), ||D_i^{-1}||_F in cond[e * cond_es + block]. The Frobenius norm bounds
+// 1 / sigma_min(D_i) from above and below within sqrt(n): a level of the block delta from E shows
+// up as ~1/delta, which the largest entry (weighted by the level's eigenvector, ~1/n per entry)
+// understates.
 __global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const int32_t* piv,
-                             int64_t piv_es, float* growth) {
+                             int64_t piv_es, float* growth, float* cond, int64_t cond_es) {
   extern __shared__ unsigned char smem[];
   const GJProb P = probs[blockIdx.x];
   const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
@@ -360,16 +364,29 @@ __global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const in
       if (p != j) { int t = idx[j]; idx[j] = idx[p]; idx[p] = t; }
     }
   __syncthreads();
-  double mx = 0.0;
+  double mx = 0.0, ss = 0.0;
   for (int r = 0; r < n; ++r) {
     c64* row = A + (int64_t)r * ld;
     for (int c = tid; c < n; c += blockDim.x) {
       buf[c] = row[c];
       mx = fmax(mx, fabs(buf[c].x) + fabs(buf[c].y));
+      ss = fma(buf[c].x, buf[c].x, fma(buf[c].y, buf[c].y, ss));
     }
     __syncthreads();
     for (int c = tid; c < n; c += blockDim.x) row[c] = buf[idx[c]];
     __syncthreads();
+  }
+  if (cond) {   // block sum of squares: warp shuffles, then one slot per warp (buf is free now)
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    double* red = reinterpret_cast<double*>(smem);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      const double f = sqrt(t);
+      cond[e * cond_es + blockIdx.x] = (f == f && f < 3.0e38) ? (float)f : __int_as_float(0x7f800000);
+    }
   }
   if (growth) {
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -687,11 +704,13 @@ cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int
 }
 
 cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
-                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth) {
-  size_t sm = (size_t)max_n * (sizeof(c64) + sizeof(int));
+                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth,
+                              float* cond, int64_t cond_es) {
+  // row buffer and column map; at least 8 doubles for the norm reduction of the 8 warps
+  size_t sm = std::max<size_t>((size_t)max_n * (sizeof(c64) + sizeof(int)), 8 * sizeof(double));
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_gj_colperm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gj_colperm<<<dim3(nmat, ne), 256, sm, s>>>(probs, F, f_es, piv, piv_es, growth);
+  k_gj_colperm<<<dim3(nmat, ne), 256, sm, s>>>(probs, F, f_es, piv, piv_es, growth, cond, cond_es);
   return cudaGetLastError();
 }
 

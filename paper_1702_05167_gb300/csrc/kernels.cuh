@@ -20,7 +20,8 @@ cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int
                            const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
                            int ne, cudaStream_t s);
 cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
-                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth = nullptr);
+                              const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth = nullptr,
+                              float* cond = nullptr, int64_t cond_es = 0);
 cudaError_t launch_residual(int64_t n, const int64_t* rowptr, const c64* hval, const int64_t* loc,
                            const int64_t* doff, const int32_t* unk_slot, const double* E, double eta,
                            const c64* sr, int64_t ncs, const c64* G, int64_t aug_es, float* resid,

@@ -12,6 +12,13 @@
 // contents; the error flag is cleared at the start of each call, everything else is written before
 // it is read. Calls whose work overlaps on the GPU (different streams, or different host threads)
 // race on the array and must be serialised by the caller.
+//
+// The library's translation units are separate CUDA modules, and under lazy module loading (the
+// CUDA 12+ default) the array comes into existence when this module is first used on a device, not
+// when the library is loaded. The first call on each device therefore loads the module and looks up
+// the array's address; a call with batch = 0 does only that, so a caller can make it before its
+// memory pool reserves the free device memory and before any stream capture.
+#include <atomic>
 #include <cstring>
 
 #include "ctx.h"
@@ -31,11 +38,14 @@ constexpr size_t NA_PIV_BYTES = ((NA_MAX_ROWS * sizeof(int32_t) + 255) / 256) * 
 constexpr size_t NA_MR_BYTES = (size_t)NA_MAX_ROWS * 2 * NA_NB * sizeof(c64);
 constexpr size_t NA_BYTES = NA_FLAG_BYTES + NA_GJ_BYTES + NA_GP_BYTES + NA_PIV_BYTES + NA_MR_BYTES;
 
-// 4.3 MiB of device scratch, resident on every device that loads the library until process exit.
+// 4.3 MiB of device scratch, resident on a device from the first call there until process exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
+// Device address of the array per device, looked up once (host threads may race on the lookup; they
+// store the same value). The cache does not survive cudaDeviceReset: after a reset the address is
+// stale, so a process that resets a device must not call this entry point on it again.
 constexpr int NA_MAX_DEVICES = 64;
-static unsigned char* g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
+static std::atomic<unsigned char*> g_scratch_ptr[NA_MAX_DEVICES];
 
 __global__ void k_na_setup(GJProb* gj, int n, int batch) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,7 +84,8 @@ using namespace hsc;
 
 extern "C" int hsc_block_inverse_noalloc(int32_t n, int32_t batch, const hsc_c128* A,
                                          hsc_c128* Ainv, void* cuda_stream) {
-  if (n <= 0 || batch <= 0 || !A || !Ainv) return hsc_fail(nullptr, HSC_ERR_ARG, "bad arguments");
+  if (n <= 0 || batch < 0 || (batch > 0 && (!A || !Ainv)))
+    return hsc_fail(nullptr, HSC_ERR_ARG, "bad arguments");
   if (n > NA_MAX_N || batch > NA_MAX_BATCH || (int64_t)n * batch > NA_MAX_ROWS)
     return hsc_fail(nullptr, HSC_ERR_ARG,
                     "block inverse without allocation supports n <= 1024, batch <= 256 and "
@@ -82,14 +93,16 @@ extern "C" int hsc_block_inverse_noalloc(int32_t n, int32_t batch, const hsc_c12
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
     return hsc_fail(nullptr, HSC_ERR_CUDA, "no usable current device");
-  if (!g_scratch_ptr[dev]) {   // once per device, with that device current
+  unsigned char* base = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!base) {   // once per device, with that device current: loads this module, finds the array
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return hsc_fail(nullptr, HSC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    base = static_cast<unsigned char*>(p);
+    g_scratch_ptr[dev].store(base, std::memory_order_release);
   }
-  unsigned char* base = g_scratch_ptr[dev];
+  if (batch == 0) return HSC_OK;   // set-up only
   int* flag = reinterpret_cast<int*>(base);
   GJProb* gj = reinterpret_cast<GJProb*>(base + NA_FLAG_BYTES);
   GemmProb* gp = reinterpret_cast<GemmProb*>(base + NA_FLAG_BYTES + NA_GJ_BYTES);

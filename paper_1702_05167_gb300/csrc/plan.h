@@ -91,6 +91,10 @@ struct Input {
   const int32_t* contact_sites = nullptr;
   int dims[3] = {0, 0, 0};   // all zero: general graph bisection
   int variant = 0;           // 1..4: alternate separator trees (cuts below the root moved +1, -1, +2, -2)
+  // geometric dissection only: 1 = contact-connected (the transport axis x is cut once, at the root;
+  // every deeper cut is a y or z plane, so each box below the root keeps its share of the x = 0 or
+  // x = Nx-1 end plane); 0 = the longest extent is cut at every level
+  int contact_connected = 0;
   const char* contact_dense = nullptr;   // per contact (nullable): 1 = one cluster on top of the tree
   // clusters (ids of the tree built without merges) whose own unknowns join their parent's
   const int32_t* merge = nullptr;

@@ -137,9 +137,13 @@ struct DeviceState {
   // (largest |(A G^r - I)_uu|); one allocation, resid = growth + growth_cap
   float* growth = nullptr;
   float* resid = nullptr;
+  float* cond = nullptr;             // per (energy, block in gj order): ||D_i^{-1}||_F, after resid
   int64_t growth_cap = 0, growth_n = 0;
   float* growth_wave = nullptr;      // the current wave's slices
   float* resid_wave = nullptr;
+  float* cond_wave = nullptr;
+  int ncl = 0;                       // clusters (blocks per energy of the cond record)
+  std::vector<int> gj_owner;         // cluster id of each Gauss-Jordan block (gj order)
   void* rs_buf = nullptr;            // device staging of re-solved energies (device-io solves)
   size_t rs_cap = 0;
   std::vector<void*> fixed;          // energy-independent allocations
@@ -295,6 +299,8 @@ int build_schedule(hsc_ctx* h) {
   }
   d->aug_es = P.tot_aug;
   d->sq_es = P.tot_sq;
+  d->ncl = nc;
+  d->gj_owner.clear();
   d->x_es = std::max<int64_t>(xs, 1);
   d->piv_es = std::max<int64_t>(P.n, 1);
 
@@ -359,6 +365,7 @@ int build_schedule(hsc_ctx* h) {
         U.asm_bytes += L.lesser ? 2 * b : b;
       }
       lcs.push_back(L);
+      d->gj_owner.push_back(i);
       GJProb g{};
       g.n = L.n; g.ld = L.n + L.m; g.off = L.aug; g.piv_off = L.own0;
       g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * nb;
@@ -794,7 +801,7 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
     }
     LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
            launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s,
-                             d->growth_wave));
+                             d->growth_wave, d->cond_wave ? d->cond_wave + U.gj : nullptr, d->ncl));
     GEMM(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0);
     schur = true;
     GEMM(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es);
@@ -1030,11 +1037,13 @@ int ensure_growth(hsc_ctx* h, int64_t n_E) {
     if (d->growth) cudaFree(d->growth);
     d->growth = nullptr;
     d->growth_cap = 0;
-    cudaError_t e = cudaMalloc((void**)&d->growth, 2 * std::max<int64_t>(n_E, 1) * sizeof(float));
+    cudaError_t e = cudaMalloc((void**)&d->growth,
+                               (2 + (int64_t)d->ncl) * std::max<int64_t>(n_E, 1) * sizeof(float));
     if (e != cudaSuccess) { cudaGetLastError(); return hsc_fail(h, HSC_ERR_OOM, "cudaMalloc growth"); }
     d->growth_cap = std::max<int64_t>(n_E, 1);
   }
   d->resid = d->growth + d->growth_cap;
+  d->cond = d->resid + d->growth_cap;
   d->growth_n = n_E;
   return HSC_OK;
 }
@@ -1053,6 +1062,7 @@ int enqueue_device(hsc_ctx* h, int64_t n_E, int64_t wave, const double* E, doubl
     const int ne = (int)std::min<int64_t>(wave, n_E - e0);
     d->growth_wave = d->growth + e0;
     d->resid_wave = d->resid + e0;
+    d->cond_wave = d->cond + e0 * d->ncl;
     d->dense_e0 = e0;
     const c64* dsr = sigma_r ? reinterpret_cast<const c64*>(sigma_r) + e0 * ncs : nullptr;
     const c64* dsl = sigma_less ? reinterpret_cast<const c64*>(sigma_less) + e0 * ncs : nullptr;
@@ -1245,6 +1255,7 @@ extern "C" int hsc_solve(hsc_t h, int64_t n_E, const double* E, double eta, cons
       const int ne = (int)std::min<int64_t>(wave, n_E - e0);
       d->growth_wave = d->growth + e0;
       d->resid_wave = d->resid + e0;
+      d->cond_wave = d->cond + e0 * d->ncl;
       d->dense_e0 = e0;
       CK(cudaMemcpyAsync(sE, E + e0, ne * 8, cudaMemcpyHostToDevice, s));
       if (ncs > 0) {
@@ -1491,6 +1502,21 @@ int read_record(hsc_ctx* h, int64_t n_E, double* out, bool residual) {
 }  // namespace hsc
 
 extern "C" int hsc_growth(hsc_t h, int64_t n_E, double* out) { return hsc::read_record(h, n_E, out, false); }
+
+extern "C" int hsc_cluster_growth(hsc_t h, int64_t n_E, double* out) {
+  using namespace hsc;
+  if (!h || (!out && n_E > 0) || n_E < 0) return hsc_fail(h, HSC_ERR_ARG, "bad arguments");
+  DeviceState* d = h->dev;
+  if (!d || !d->growth || n_E > d->growth_n)
+    return hsc_fail(h, HSC_ERR_STATE, "no solve of that many energies has run on this handle");
+  const int nc = d->ncl;
+  std::vector<float> g((size_t)n_E * nc);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(g.data(), d->cond, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < n_E; ++k)
+    for (int j = 0; j < nc; ++j) out[k * nc + d->gj_owner[j]] = g[k * nc + j];
+  return HSC_OK;
+}
 extern "C" int hsc_residual(hsc_t h, int64_t n_E, double* out) { return hsc::read_record(h, n_E, out, true); }
 
 // ---- batched solve in one CUDA graph -----------------------------------------------------------

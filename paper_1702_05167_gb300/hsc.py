@@ -21,14 +21,14 @@ EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_b
            "hsc_tune", "hsc_set_option", "hsc_get_option", "hsc_set_contact_dense", "hsc_solve_dense",
            "hsc_set_merge",
            "hsc_profile",
-           "hsc_profile_read", "hsc_growth",
+           "hsc_profile_read", "hsc_growth", "hsc_cluster_growth",
            "hsc_residual",
            "hsc_device_fp64_peaks", "hsc_observables", "hsc_scba", "hsc_last_error", "hsc_destroy",
            "hsc_mlp_create", "hsc_mlp_num_params", "hsc_mlp_set_params", "hsc_mlp_get_params",
            "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF, HSC_OPT_COMPLEX_4M = 1, 2, 3, 4, 5
 HSC_OPT_FP64_ENGINE, HSC_OPT_RESOLVE_DIGITS, HSC_OPT_TREE_VARIANT, HSC_OPT_ORDERING = 6, 7, 8, 9
-HSC_OPT_MAX_CLUSTER = 10
+HSC_OPT_MAX_CLUSTER, HSC_OPT_TREE_FORM = 10, 11
 
 
 class hsc_tree_stats(ctypes.Structure):
@@ -113,6 +113,7 @@ def load():
     L.hsc_mlp_destroy.argtypes = [vp]
     L.hsc_profile.argtypes = [vp, i32]
     L.hsc_growth.argtypes = [vp, i64, vp]
+    L.hsc_cluster_growth.argtypes = [vp, i64, vp]
     L.hsc_residual.argtypes = [vp, i64, vp]
     L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(hsc_kernel_stat), i32, ctypes.POINTER(i32)]
     L.hsc_device_fp64_peaks.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
@@ -316,6 +317,13 @@ def hsc_growth(h, n_E):
     return out
 
 
+def hsc_cluster_growth(h, n_E, n_clusters):
+    """Per-energy, per-cluster ||D_i^{-1}||_F of the last solve (n_E x n_clusters, postorder ids)."""
+    out = np.zeros((n_E, n_clusters))
+    _check(h, load().hsc_cluster_growth(h, int(n_E), _ptr(out)))
+    return out
+
+
 def hsc_residual(h, n_E):
     """Per-energy residual of the last solve: max_u |(A G^r - I)_uu| from the computed blocks."""
     out = np.zeros(n_E)
@@ -345,8 +353,18 @@ def hsc_device_fp64_peaks():
 
 
 def hsc_block_inverse_noalloc(n, batch, A, Ainv, stream=None):
-    """Invert `batch` n x n complex128 device blocks (torch float64 tensors holding interleaved
-    re/im) with the library's allocation-free entry point."""
+    """Invert `batch` n x n complex128 device blocks (torch float64 or complex128 CUDA tensors,
+    interleaved re/im) with the library's allocation-free entry point. batch = 0 only sets up the
+    current device's scratch (A and Ainv may be None)."""
+    if int(batch) > 0:
+        if A is None or Ainv is None:
+            raise ValueError("A and Ainv are required when batch > 0")
+        _check_io(True, A=A, Ainv=Ainv)
+        need = int(batch) * int(n) * int(n) * 16
+        for name, t in (("A", A), ("Ainv", Ainv)):
+            have = t.numel() * t.element_size()
+            if have < need:
+                raise ValueError(f"{name} holds {have} bytes, {need} needed for {batch} blocks of {n} x {n}")
     L = load()
     L.hsc_block_inverse_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p]
@@ -425,10 +443,12 @@ def hsc_destroy(h):
 class Solver:
     """Convenience owner of one handle for a workloads.Device (create + analyze)."""
 
-    def __init__(self, dev, leaf_max, geometric=True):
+    def __init__(self, dev, leaf_max, geometric=True, ordering=None):
         self.dev = dev
         self.h = hsc_create(dev.n, dev.orb, dev.rowptr, dev.col, dev.val, dev.contact_ptr,
                             dev.contact_sites, dev.dims if geometric else None)
+        if ordering is not None:
+            hsc_set_option(self.h, HSC_OPT_ORDERING, ordering)
         self.stats = hsc_analyze(self.h, leaf_max)
 
     def solve(self, E, eta, sigma_r, sigma_less=None, precision=HSC_FP64, pairs=None):

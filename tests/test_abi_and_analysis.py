@@ -166,9 +166,10 @@ def test_set_contact_dense_checks_arguments_and_requires_a_new_analysis():
                                            ((9, 8, 7), 2, False)])
 def test_alternate_trees_share_the_root_and_move_the_leaves(dims, leaf, geo):
     """The alternate separator trees keep the root separator (so the coupling entries across it
-    stay in the selected pattern) and change the leaf clusters (different isolated blocks)."""
+    stay in the selected pattern) and change the leaf clusters (different isolated blocks); shown
+    on the plain geometric tree, whose deeper cuts run along every axis."""
     dev = W.cubic_device(dims, seed=2)
-    trees = [_tree(dev, leaf, geo, v)[1] for v in (0, 1, 2, 3, 4)]
+    trees = [_tree(dev, leaf, geo, v, ordering=2 if geo else None)[1] for v in (0, 1, 2, 3, 4)]
     roots = [set(t[-1][1].tolist()) for t in trees]
     assert all(r == roots[0] for r in roots)
     leaves = [{frozenset(own.tolist()) for info, own, _ in t if info.child[0] < 0 and info.child[1] < 0}
@@ -242,8 +243,9 @@ def test_graph_ordering_option_matches_a_handle_without_grid_dims():
     st = hsc.hsc_analyze(h, 2)
     cl = [hsc.hsc_cluster(h, i) for i in range(st.n_clusters)]
     with pytest.raises(hsc.HSCError) as ei:
-        hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 2)
+        hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 3)
     assert ei.value.code == hsc.HSC_ERR_ARG
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_TREE_FORM) == 2
     hsc.hsc_destroy(h)
     st2, cl2 = _tree(dev, 2, geometric=False)
     assert st.n_clusters == st2.n_clusters and st.flops_gr == st2.flops_gr
@@ -254,7 +256,7 @@ def test_graph_ordering_option_matches_a_handle_without_grid_dims():
 def test_degenerate_chain_tree():
     """A 1D chain with leaves of one site: every cluster is one unknown and every update set has at
     most two entries (the separator structure that makes HSC coincide with RGF, Section 2.2)."""
-    st, cl = _tree(W.chain_device(31), 1)
+    st, cl = _tree(W.chain_device(31), 1, ordering=2)
     assert st.max_n == 1 and st.max_m <= 2
 
 
@@ -326,14 +328,55 @@ def test_binding_rejects_buffers_of_the_wrong_kind_before_the_call():
         hsc.hsc_solve(h, torch.from_numpy(E).float(), 1e-6, sr, sl, hsc.HSC_FP64, None, out, out.copy(),
                       None, None)
     hsc.hsc_destroy(h)
+    blocks = torch.zeros(2 * 4 * 4 * 2, dtype=torch.float64)   # host memory: refused for device I/O
+    with pytest.raises(ValueError):
+        hsc.hsc_block_inverse_noalloc(4, 2, blocks, blocks)
+    with pytest.raises(ValueError):
+        hsc.hsc_block_inverse_noalloc(4, 2, None, None)
+
+
+FLOPS_CC = (427439805056.0, 272819044952.0)   # model flops per energy, contact-connected 32^3 tree
 
 
 def test_metric_workload_tree_is_unchanged():
-    """The 32^3 workload's tree (leaves <= 8) and its model: 127 clusters over 7 levels, largest
-    front 1024 x 2048, 179.5 + 189.6 GFLOP per energy (the figures the measurements use)."""
+    """The 32^3 workload's trees (leaf_max 8) and their models, the figures the measurements use:
+    the default contact-connected tree (x cut once, 15/16 x 8 x 8 leaves): 63 clusters over 6
+    levels; the plain geometric tree (8^3 leaves): 127 clusters over 7 levels, 179.5 + 189.6 GFLOP
+    per energy."""
     dev = W.cubic_device((32, 32, 32), seed=0)
     h = _handle(dev)
     st = hsc.hsc_analyze(h, 8)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_TREE_FORM) == 1
+    assert (st.n_clusters, st.n_heights, st.n_depths, st.max_n, st.max_m) == (63, 6, 6, 1024, 1024)
+    assert abs(st.flops_gr - FLOPS_CC[0]) <= 1.0 and abs(st.flops_gl - FLOPS_CC[1]) <= 1.0
+    hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 2)
+    st = hsc.hsc_analyze(h, 8)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_TREE_FORM) == 0
     hsc.hsc_destroy(h)
     assert (st.n_clusters, st.n_heights, st.n_depths, st.max_n, st.max_m) == (127, 7, 7, 1024, 1024)
     assert abs(st.flops_gr - 179528180960.0) <= 1.0 and abs(st.flops_gl - 189624310312.0) <= 1.0
+
+
+def test_contact_connected_tree_keeps_every_box_on_a_contact_face():
+    """Contact-connected dissection (the default for contacts on the end planes x = 0 and
+    x = Nx-1): the root is the one x plane; every other cluster is a y or z cut or a leaf box
+    spanning half the device in x, so each of them holds sites of an end plane; the tree is exact.
+    An elongated device keeps the plain form (model cost above 3x)."""
+    for dims, leaf in (((12, 9, 7), 3), ((9, 8, 8), 4), ((16, 5, 11), 2)):
+        dev = W.cubic_device(dims, seed=1)
+        st, cl = _tree(dev, leaf)
+        _check_tree(dev, cl)
+        Nx, Ny, Nz = dims
+        x_of = lambda own: own // (Ny * Nz)   # noqa: E731  (one orbital per site)
+        root = cl[-1][1]
+        assert len(set(x_of(root).tolist())) == 1 and len(root) == Ny * Nz
+        for info, own, upd in cl[:-1]:
+            xs = set(x_of(own).tolist())
+            assert 0 in xs or Nx - 1 in xs, (dims, info.n)
+            if info.child[0] < 0:
+                assert max(np.ptp((own % (Ny * Nz)) // Nz), np.ptp(own % Nz)) < leaf
+    wire = W.wire_device((64, 12, 12), orb=2, seed=0)
+    h = _handle(wire)
+    hsc.hsc_analyze(h, 4)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_TREE_FORM) == 0
+    hsc.hsc_destroy(h)

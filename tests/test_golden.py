@@ -1,4 +1,4 @@
-"""The dense oracle still reproduces the frozen 8x8x8 fixture (see tests/golden/README.md)."""
+"""The dense oracle still reproduces the frozen 8x8x8 fixture written by tests/golden/make_golden.py."""
 import os
 import sys
 

@@ -117,6 +117,7 @@ def test_merging_high_growth_clusters_recovers_the_lost_digits():
     L = dense.embed_diag(dev.n, idx, sl[0])
     gd = np.diag(np.linalg.inv(A))
     h = _handle(dev)
+    hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, 2)   # the plain geometric tree, which meets the level
     st = hsc.hsc_analyze(h, 3)
     base = tree(h, st.n_clusters)
     parents = [hsc.hsc_cluster(h, i, want_sets=False)[0].parent for i in range(st.n_clusters)]

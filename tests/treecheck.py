@@ -10,8 +10,10 @@ def _handle(dev, geometric=True):
                           dev.contact_sites, dev.dims if geometric else None)
 
 
-def _tree(dev, leaf, geometric=True, variant=0, dense=()):
+def _tree(dev, leaf, geometric=True, variant=0, dense=(), ordering=None):
     h = _handle(dev, geometric)
+    if ordering is not None:
+        hsc.hsc_set_option(h, hsc.HSC_OPT_ORDERING, ordering)
     if variant:
         hsc.hsc_set_option(h, hsc.HSC_OPT_TREE_VARIANT, variant)
     for c in dense:
