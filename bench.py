@@ -405,6 +405,7 @@ def run_hsc(args):
         s48r, s48l = W.self_energies(d48, 4)
         sv = hsc.Solver(d48, 8)
         hsc.hsc_set_option(sv.h, hsc.HSC_OPT_FP64_LEVELS, 0)
+        hsc.hsc_set_option(sv.h, hsc.HSC_OPT_RESOLVE_DIGITS, 0)
         sv.solve(E48[:1], cfg["eta"], s48r[:1], s48l[:1], precision=hsc.HSC_MIXED)
         hsc.hsc_profile(sv.h, True)
         sv.solve(E48, cfg["eta"], s48r, s48l, precision=hsc.HSC_MIXED)
@@ -417,6 +418,7 @@ def run_hsc(args):
         work = 3 * sc["flops"] / (sc["ms"] / 1000.0) / 1e12 if sc["ms"] > 0 else 0.0
         # the same Schur updates in the FP64 path: FP64 emulation on the BF16 tensor cores
         sv = hsc.Solver(d48, 8)
+        hsc.hsc_set_option(sv.h, hsc.HSC_OPT_RESOLVE_DIGITS, 0)   # the Schur kernels of one tree only
         sv.solve(E48[:1], cfg["eta"], s48r[:1], s48l[:1])
         hsc.hsc_profile(sv.h, True)
         sv.solve(E48, cfg["eta"], s48r, s48l)
@@ -447,6 +449,7 @@ def run_hsc(args):
     plain_out = {}
     if rank == 0 and not args.no_plain and args.ordering == "geometric":
         sp = hsc.Solver(dev, cfg["leaf"], True, ordering=2)
+        hsc.hsc_set_option(sp.h, hsc.HSC_OPT_RESOLVE_DIGITS, 4)   # the former default threshold
         def step_p():
             hsc.hsc_solve(sp.h, tE, cfg["eta"], tsr, tsl, hsc.HSC_FP64, pairs, ogr2, ogl2, pgr2, pgl2,
                           stream=stream.cuda_stream, io_on_device=True)
@@ -468,7 +471,7 @@ def run_hsc(args):
         sp.close()
         plain = {"value": nE / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                  "tree": "plain geometric dissection, 8^3 leaves (HSC_OPT_ORDERING = 2), "
-                         "residual re-solve on alternate trees (default)",
+                         "residual re-solve above 1e-4 on its alternate trees",
                  "clusters": pst.n_clusters, "model_gflop_per_energy": (pst.flops_gr + pst.flops_gl) / 1e9,
                  "residual_max": float(pres.max()), "residual_median": float(np.median(pres)),
                  "energies_residual_gt_1e-4": int((pres > 1e-4).sum()),
@@ -512,8 +515,8 @@ def run_hsc(args):
                            "precision": "complex128 (HSC_FP64)", "io": "device-resident",
                            "fp64_engine": "per product list by cost model: FP64 tensor pipe or FP64 "
                                           "emulation on the BF16 tensor cores (HSC_OPT_FP64_ENGINE = 0)",
-                           "resolve": "energies with residual |(A G^r - I)_uu| > 1e-4 re-solved on "
-                                      "alternate separator trees (HSC_OPT_RESOLVE_DIGITS = 4, default)",
+                           "resolve": "energies with residual |(A G^r - I)_uu| > 1e-10 re-solved on "
+                                      "alternate separator trees (HSC_OPT_RESOLVE_DIGITS = 10, default)",
                            "clusters": st.n_clusters,
                            "l2": "working set ~%.0f GB >> L2 (no flush needed)" % (st.bytes_per_energy * nE / 1e9),
                            "parallelism": f"energy-sharded x{ws}"},

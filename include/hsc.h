@@ -189,11 +189,13 @@ typedef enum {
                               /* slice products exactly; its error per K value is below         */
                               /* 2^-52.8 times the two scales, at the level of FP64 rounding.   */
   HSC_OPT_RESOLVE_DIGITS = 7, /* d > 0: hsc_solve solves every energy whose residual (see      */
-                              /* hsc_residual) exceeds 10^-d again on the alternate separator   */
+                              /* hsc_residual; default d = 10: on the 32^3 cube at eta = 1e-6   */
+                              /* the default tree leaves 3 of 64 energies above 1e-10, the      */
+                              /* median is 1e-11) exceeds 10^-d again on the alternate separator*/
                               /* trees in turn (the root plane kept, every deeper cut moved by  */
                               /* +1, -1, +2, -2 planes; an energy goes to the next tree while   */
                               /* still above the threshold) and keeps, per energy, the result   */
-                              /* with the smallest residual; 0 = off; default 4. HSC_FP64 solves */
+                              /* with the smallest residual; 0 = off. HSC_FP64 solves          */
                               /* only (a mixed-precision residual reflects its FP32 rounding).  */
                               /* Each alternate tree is analysed on first need and works in the */
                               /* handle's own workspace after the first pass.                   */
@@ -276,8 +278,10 @@ typedef struct {
  *   when smaller than the grid) and Gauss-Jordan panel width (16, 32, 64) re-analyse, solve the given
  *   probe energies twice (host buffers, as hsc_solve, residual re-solve included) and time the
  *   second solve with CUDA events (give it probes spread over the energy window: whether a probe
- *   needs a re-solve on a given tree weighs in its time);
- *   keep the fastest, leave the handle analysed with it, and append one JSON line (GPU name, grid,
+ *   needs a re-solve on a given tree weighs in its time). A candidate whose worst probe residual
+ *   (HSC_FP64) exceeds the handle's re-solve threshold 10^-d is not admissible (a smaller leaf
+ *   loses digits at small eta); keep the fastest admissible candidate (if none is, the one with the
+ *   smallest worst residual), leave the handle analysed with it, and append one JSON line (GPU name, grid,
  *   orbitals, precision, choice, time) to cache_path (may be NULL: no cache). A matching cache line
  *   is applied without timing. Errors: as hsc_analyze / hsc_solve. */
 int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const hsc_c128* sigma_r,

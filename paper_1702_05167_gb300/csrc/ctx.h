@@ -34,7 +34,7 @@ struct hsc_ctx {
   int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe
   int opt_4m = 0;             // FP64 engine: 4 real products per complex product (default 3)
   int opt_fp64_engine = 0;    // FP64-accurate products: 0 cost model, 1 FP64 pipe, 2 emulation
-  int opt_resolve = 4;        // d: re-solve energies whose residual exceeds 10^-d (0: off)
+  int opt_resolve = 10;       // d: re-solve energies whose residual exceeds 10^-d (0: off)
   int opt_ordering = 0;       // 0: geometric (contact-connected for end-plane contacts), 1: graph
                               // bisection, 2: plain geometric (longest extent at every level)
   int tree_form = -1;         // tree of the last analyze: 0 plain geometric, 1 contact-connected,

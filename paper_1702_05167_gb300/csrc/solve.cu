@@ -1717,8 +1717,15 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
   for (int l : {4, 6, 8})
     if (l < maxdim) leaves.push_back(l);
   if (leaves.empty()) leaves.push_back(h->leaf_max > 0 ? h->leaf_max : 4);
-  double best = 1e300;
+  // a candidate is admissible when every probe's residual (after the solve's own re-solves) stays
+  // within the handle's threshold 10^-d (HSC_OPT_RESOLVE_DIGITS, or 1e-10 when re-solves are off):
+  // a cheaper tree that loses digits is not a faster solve of the same problem. The fastest
+  // admissible candidate wins; if none is admissible, the one with the smallest worst residual.
+  const double thr = std::pow(10.0, -(h->opt_resolve > 0 ? h->opt_resolve : 10));
+  double best = 1e300, best_res = 1e300;
+  bool best_ok = false;
   int best_leaf = leaves[0], best_nb = 32, tried = 0;
+  std::vector<double> res(n_E);
   (void)ncs;
   for (int leaf : leaves)
     for (int nb : {16, 32, 64}) {
@@ -1742,8 +1749,14 @@ extern "C" int hsc_tune(hsc_t h, int64_t n_E, const double* E, double eta, const
       cudaEventDestroy(b);
       if (rc != HSC_OK) return rc;
       ++tried;
-      if (ms < best) {
+      double rmax = 0.0;
+      if (precision == HSC_FP64 && hsc_residual(h, n_E, res.data()) == HSC_OK)
+        for (double r : res) rmax = std::max(rmax, r);
+      const bool ok = rmax <= thr;
+      if ((ok && (!best_ok || ms < best)) || (!ok && !best_ok && rmax < best_res)) {
         best = ms;
+        best_res = rmax;
+        best_ok = ok;
         best_leaf = leaf;
         best_nb = nb;
       }

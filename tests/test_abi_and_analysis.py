@@ -291,7 +291,7 @@ def test_options_round_trip_and_reject_bad_values():
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF) == 2
     hsc.hsc_set_option(h, hsc.HSC_OPT_GJ_PANEL, 8)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_GJ_PANEL) == 8
-    assert hsc.hsc_get_option(h, hsc.HSC_OPT_RESOLVE_DIGITS) == 4
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_RESOLVE_DIGITS) == 10
     hsc.hsc_set_option(h, hsc.HSC_OPT_FP64_ENGINE, 2)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_FP64_ENGINE) == 2
     hsc.hsc_set_option(h, hsc.HSC_OPT_RESOLVE_DIGITS, 8)
