@@ -288,8 +288,8 @@ def run_hsc(args):
     tot_ms = sum(p["ms"] for p in prof)
     cls = lambda names: {k: sum(p[k] for p in prof if p["name"] in names)
                          for k in ("flops", "ms", "timed", "launches")}
-    gz = cls(("gemm_z_dmma", "schur_z_dmma"))
-    go = cls(("gemm_z_ozaki", "schur_z_ozaki"))
+    gz = cls(("gemm_z_dmma", "schur_z_dmma", "gj_update_dmma"))
+    go = cls(("gemm_z_ozaki", "schur_z_ozaki", "gj_update_ozaki"))
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -354,7 +354,7 @@ def run_hsc(args):
         got_gl = mgl.cpu().numpy().view(np.complex128)
         rel = lambda a, b: np.abs(a - b).max(axis=1) / np.abs(b).max(axis=1)
         eg, el = rel(got_gr, ref_gr), rel(got_gl, ref_gl)
-        tcp = {k: sum(p[k] for p in mprof if p["name"] in ("gemm_tc_tf32x3", "schur_tc_tf32x3"))
+        tcp = {k: sum(p[k] for p in mprof if p["name"] in ("gemm_tc_tf32x3", "schur_tc_tf32x3", "gj_update_tc"))
                for k in ("flops", "ms", "launches")}
         mixed = {"value": nE / (mms / 1000.0), "unit": UNIT, "ms_per_step": mms,
                  "max_rel_err_vs_fp64_path": {"diag_gr": float(eg.max()), "diag_gl": float(el.max()),

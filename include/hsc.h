@@ -223,6 +223,12 @@ typedef enum {
                               /* into a chain of pieces of at most that many sites, each the    */
                               /* parent of the previous (Section 3.4's degenerate sub-trees for */
                               /* dense molecular blocks); dense contacts stay whole; 0 = off    */
+  HSC_OPT_GJ_WIDE = 12,       /* nested blocking of the Gauss-Jordan inversion: the panels of    */
+                              /* HSC_OPT_GJ_PANEL width are reduced inside a wide panel of this  */
+                              /* width (rounded down to a multiple of the panel width), whose    */
+                              /* columns alone their products update; one trailing product with */
+                              /* K = this width then updates the rest of the block (default 128; */
+                              /* 0 or <= the panel width: every panel updates the whole block)   */
   HSC_OPT_TREE_FORM = 11      /* read only: the tree of the last hsc_analyze: 0 plain geometric,*/
                               /* 1 contact-connected geometric, 2 graph bisection (-1 before    */
                               /* any analysis). With HSC_OPT_ORDERING = 0 the contact-connected */

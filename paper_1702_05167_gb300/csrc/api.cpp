@@ -213,6 +213,10 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       if (value < 1 || value > 64) return hsc_fail(h, HSC_ERR_ARG, "panel width must be in [1, 64]");
       h->opt_nb = value;
       break;
+    case HSC_OPT_GJ_WIDE:
+      if (value < 0 || value > 512) return hsc_fail(h, HSC_ERR_ARG, "wide panel width must be in [0, 512]");
+      h->opt_nbo = value;
+      break;
     case HSC_OPT_FP64_LEVELS:
       if (value < 0) return hsc_fail(h, HSC_ERR_ARG, "levels must be >= 0");
       h->opt_fp64_levels = value;
@@ -256,6 +260,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
   if (!h || !value) return hsc_fail(h, HSC_ERR_ARG, "NULL argument");
   switch (option) {
     case HSC_OPT_GJ_PANEL: *value = h->opt_nb; break;
+    case HSC_OPT_GJ_WIDE: *value = h->opt_nbo; break;
     case HSC_OPT_FP64_LEVELS: *value = h->opt_fp64_levels; break;
     case HSC_OPT_MIXED_GJ_FP64: *value = h->opt_gj_fp64; break;
     case HSC_OPT_LEAF: *value = h->leaf_max; break;
@@ -329,6 +334,7 @@ hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
   a->contact_dense = h->contact_dense;
   std::memcpy(a->dims, h->dims, sizeof(a->dims));
   a->opt_nb = h->opt_nb;
+  a->opt_nbo = h->opt_nbo;
   a->opt_fp64_levels = h->opt_fp64_levels;
   a->opt_gj_fp64 = h->opt_gj_fp64;
   a->opt_4m = h->opt_4m;

@@ -318,13 +318,15 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
     }
 }
 
-// apply the panel's row swaps to every column outside the panel and copy its pivot rows to R
+// apply the panel's row swaps to the columns [c_lo, c_hi) outside the panel and copy its pivot
+// rows there to R (all columns for a whole-matrix step; the enclosing wide panel's columns for a
+// step nested inside it)
 __global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32_t* piv,
-                          int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb) {
+                          int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb, int c_lo, int c_hi) {
   const GJProb P = probs[blockIdx.y];
   const int e = blockIdx.z, n = P.n, ld = P.ld;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n || c >= n) return;
+  const int c = c_lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n || c >= n || c >= c_hi) return;
   const int w = min(nb, n - k0);
   if (c >= k0 && c < k0 + w) return;
   c64* A = F + e * f_es + P.off;
@@ -339,6 +341,28 @@ __global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32
   }
   c64* R = Rt + e * t_es + P.rt_off;
   for (int t = 0; t < w; ++t) R[(int64_t)t * n + c] = A[(int64_t)(k0 + t) * ld + c];
+}
+
+// The wide panel [k0, k0 + w) of each block, whose columns the nested steps have reduced, moves to
+// M (n x nb, leading dimension nb) and is zeroed in place; R (nb x n) gets the identity in those
+// columns, so that the trailing product M R restores them.
+__global__ void k_gj_move(const GJProb* probs, c64* F, int64_t f_es, c64* Mt, c64* Rt, int64_t t_es,
+                          int k0, int nb) {
+  const GJProb P = probs[blockIdx.y];
+  const int e = blockIdx.z, n = P.n, ld = P.ld;
+  if (k0 >= n) return;
+  const int w = min(nb, n - k0);
+  c64* A = F + e * f_es + P.off;
+  c64* M = Mt + e * t_es + P.mt_off;
+  c64* R = Rt + e * t_es + P.rt_off;
+  const int64_t tot = (int64_t)n * w;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / w), c = (int)(idx % w);
+    M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
+    A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
+    if (r < w) R[(int64_t)r * n + k0 + c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
 }
 
 // undo the row interchanges on the columns of the in-place inverse: A^{-1} = Y P
@@ -650,8 +674,10 @@ cudaError_t launch_add_a(const LevelCluster* lc, int nl, int64_t max_h, int max_
     dim3 g(blocks_for(max_h, 256), nl);
     k_add_h<<<g, 256, 0, s>>>(lc, h_rq, h_vi, hval, F, aug_es, ne);
   }
-  dim3 g2(blocks_for(max_n, 256), nl);
-  k_add_diag<<<g2, 256, 0, s>>>(lc, own_contact, E, eta, sr, sl, ncs, F, L, aug_es, ne);
+  if (max_n > 0) {   // a level of pass-through clusters alone (merged trees) has no own unknowns
+    dim3 g2(blocks_for(max_n, 256), nl);
+    k_add_diag<<<g2, 256, 0, s>>>(lc, own_contact, E, eta, sr, sl, ncs, F, L, aug_es, ne);
+  }
   return cudaGetLastError();
 }
 
@@ -697,9 +723,19 @@ cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es,
 
 cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
                            const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
-                           int ne, cudaStream_t s) {
-  k_gj_swap<<<dim3(blocks_for(max_n, 128), nmat, ne), 128, 0, s>>>(probs, F, f_es, piv, piv_es, Rt,
-                                                                   t_es, k0, nb);
+                           int ne, cudaStream_t s, int c_lo, int c_hi) {
+  const int hi = std::min(c_hi, max_n);
+  if (hi <= c_lo) return cudaSuccess;
+  k_gj_swap<<<dim3(blocks_for(hi - c_lo, 128), nmat, ne), 128, 0, s>>>(probs, F, f_es, piv, piv_es, Rt,
+                                                                       t_es, k0, nb, c_lo, hi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gj_move(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es, c64* Mt,
+                           c64* Rt, int64_t t_es, int k0, int nb, int ne, cudaStream_t s) {
+  if (k0 >= max_n) return cudaSuccess;
+  const int64_t tot = (int64_t)max_n * std::min(nb, max_n - k0);
+  k_gj_move<<<dim3(blocks_for(tot, 256), nmat, ne), 256, 0, s>>>(probs, F, f_es, Mt, Rt, t_es, k0, nb);
   return cudaGetLastError();
 }
 

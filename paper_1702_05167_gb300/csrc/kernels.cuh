@@ -18,7 +18,9 @@ cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es,
                             int* flag, cudaStream_t s, int cluster = 1);
 cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
                            const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
-                           int ne, cudaStream_t s);
+                           int ne, cudaStream_t s, int c_lo = 0, int c_hi = 1 << 30);
+cudaError_t launch_gj_move(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es, c64* Mt,
+                           c64* Rt, int64_t t_es, int k0, int nb, int ne, cudaStream_t s);
 cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
                               const int32_t* piv, int64_t piv_es, int ne, cudaStream_t s, float* growth = nullptr,
                               float* cond = nullptr, int64_t cond_es = 0);

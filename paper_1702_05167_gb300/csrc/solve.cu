@@ -32,6 +32,14 @@ struct GemmPair {
   bool oz_faster = false;   // cost model: the emulation beats the FP64 pipe on this list
 };
 
+// One Gauss-Jordan step of a level: kind 0 = a panel of width nb over the whole block (panel,
+// swap on every column, trailing product with K = nb); kind 1 = a panel of width nb nested in the
+// wide panel [k1, k1 + nbo) (swap and product restricted to the wide panel's columns); kind 2 = the
+// wide panel's own step (move it to M, swap every other column, trailing product with K = nbo).
+struct GjStep {
+  int kind = 0, k0 = 0, k1 = 0;
+};
+
 struct UpLevel {
   int nl = 0;
   int64_t lc = 0;           // index into the LevelCluster array
@@ -43,6 +51,8 @@ struct UpLevel {
   int64_t gj = 0;           // index into the GJProb array
   int nmat = 0;
   std::vector<GemmPair> steps;
+  std::vector<GjStep> sdesc;     // what each entry of steps is
+  int64_t gji = 0;               // index into the nested-panel GJProb array
   int dense0 = 0, dense_n = 0;   // DENSE contact blocks of this level's clusters (dense_dev range)
   int64_t dense_max = 0;         // largest nu^2 among them
 };
@@ -57,11 +67,12 @@ struct DownLevel {
 };
 
 enum KClass { K_GEMM = 0, K_GEMM_TC, K_SCHUR, K_SCHUR_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
-              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_RESID, K_NCLASS };
+              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_RESID, K_GJU, K_GJU_TC, K_GJU_OZ, K_NCLASS };
 static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "schur_z_dmma",
                                            "schur_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
                                            "assemble", "add_a", "lesser_fold", "gather", "out",
-                                           "gemm_z_ozaki", "schur_z_ozaki", "residual"};
+                                           "gemm_z_ozaki", "schur_z_ozaki", "residual",
+                                           "gj_update_dmma", "gj_update_tc", "gj_update_ozaki"};
 
 struct Prof {
   bool on = false;
@@ -81,6 +92,7 @@ struct DeviceState {
   Prof prof;
   bool planned = false;
   int nb = 32;                       // Gauss-Jordan panel width
+  int nbo = 0;                       // wide-panel width of the nested blocking (0: not nested)
   int fp64_levels = 2;               // mixed mode: top tree levels kept on the FP64 pipe
   bool gj_fp64 = false;              // mixed mode: Gauss-Jordan trailing updates on the FP64 pipe
   bool four_products = false;        // FP64 engine: 4 real products per complex product (else 3M)
@@ -90,6 +102,7 @@ struct DeviceState {
   ClusterGlobal* cg = nullptr;
   LevelCluster* lcs = nullptr;
   GJProb* gjp = nullptr;
+  GJProb* gjpi = nullptr;            // the same blocks with the nested panels' M and R buffers
   GemmProb* gp = nullptr;
   GemmProb* gp128 = nullptr;
   GemmProb* gpoz = nullptr;
@@ -288,6 +301,7 @@ int build_schedule(hsc_ctx* h) {
   const Plan& P = h->plan;
   const int nc = (int)P.cl.size();
   const int nb = d->nb;
+  const int nbo = d->nbo > nb ? d->nbo : 0;   // nested blocking when the wide panel is wider
   std::vector<ClusterGlobal> cg(nc);
   std::vector<int64_t> xoff(nc);
   int64_t xs = 0;
@@ -305,7 +319,7 @@ int build_schedule(hsc_ctx* h) {
   d->piv_es = std::max<int64_t>(P.n, 1);
 
   std::vector<LevelCluster> lcs;
-  std::vector<GJProb> gjs;
+  std::vector<GJProb> gjs, gjs_in;
   std::vector<GemmProb> gps, gps128, gpsoz;
   int64_t tt_max = 1, tz_max = 1, tn_max = 1, gjt_max = 1;
 
@@ -368,15 +382,23 @@ int build_schedule(hsc_ctx* h) {
       d->gj_owner.push_back(i);
       GJProb g{};
       g.n = L.n; g.ld = L.n + L.m; g.off = L.aug; g.piv_off = L.own0;
-      g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * nb;
-      gjt += 2 * (int64_t)L.n * nb;
+      const int wo = nbo ? nbo : nb;   // M: n x wo, R: wo x n
+      g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * wo;
+      gjt += 2 * (int64_t)L.n * wo;
       gjs.push_back(g);
+      if (nbo) {   // the nested panels' M (n x nb) and R (nb x n)
+        GJProb gi = g;
+        gi.mt_off = gjt; gi.rt_off = gjt + (int64_t)L.n * nb;
+        gjt += 2 * (int64_t)L.n * nb;
+        gjs_in.push_back(gi);
+      }
     }
     U.total = el;
     tt_max = std::max(tt_max, tt);
     tz_max = std::max(tz_max, tz);
     gjt_max = std::max(gjt_max, gjt);
     U.gj = (int64_t)gjs.size() - U.nl;
+    U.gji = nbo ? (int64_t)gjs_in.size() - U.nl : 0;
     U.nmat = U.nl;
     const LevelCluster* lv = lcs.data() + U.lc;
     {
@@ -416,15 +438,45 @@ int build_schedule(hsc_ctx* h) {
       }
       U.u4 = g4.args(OP_T, OP_N, 1, 0, 0, 0);
       const GJProb* gl = gjs.data() + U.gj;
-      for (int k0 = 0; k0 < U.max_n; k0 += nb) {
-        GemmList gs(gps, gps128, gpsoz);
-        for (int k = 0; k < U.nl; ++k) {
-          const GJProb& q = gl[k];
-          if (q.n <= k0) continue;
-          int w = std::min(nb, q.n - k0);
-          gs.add(q.n, q.n, w, q.mt_off, nb, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k0, k0 + w);
+      if (!nbo) {
+        for (int k0 = 0; k0 < U.max_n; k0 += nb) {
+          GemmList gs(gps, gps128, gpsoz);
+          for (int k = 0; k < U.nl; ++k) {
+            const GJProb& q = gl[k];
+            if (q.n <= k0) continue;
+            int w = std::min(nb, q.n - k0);
+            gs.add(q.n, q.n, w, q.mt_off, nb, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k0, k0 + w);
+          }
+          U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+          U.sdesc.push_back(GjStep{0, k0, 0});
         }
-        U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+      } else {
+        const GJProb* gi = gjs_in.data() + U.gji;
+        for (int k1 = 0; k1 < U.max_n; k1 += nbo) {
+          // nested panels: products restricted to the wide panel's columns [k1, k1 + wo)
+          for (int k0 = k1; k0 < std::min(k1 + nbo, U.max_n); k0 += nb) {
+            GemmList gs(gps, gps128, gpsoz);
+            for (int k = 0; k < U.nl; ++k) {
+              const GJProb& q = gi[k];
+              if (q.n <= k0) continue;
+              const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
+              gs.add(q.n, wo, w, q.mt_off, nb, q.rt_off + k1, q.n, q.off + k1, q.ld, q.off + k1, q.ld, 1,
+                     k0, k0 + w);
+            }
+            U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+            U.sdesc.push_back(GjStep{1, k0, k1});
+          }
+          // the wide panel's trailing product over the whole block, K = wo
+          GemmList gs(gps, gps128, gpsoz);
+          for (int k = 0; k < U.nl; ++k) {
+            const GJProb& q = gl[k];
+            if (q.n <= k1) continue;
+            const int wo = std::min(nbo, q.n - k1);
+            gs.add(q.n, q.n, wo, q.mt_off, nbo, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k1, k1 + wo);
+          }
+          U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+          U.sdesc.push_back(GjStep{2, k1, k1});
+        }
       }
     }
   }
@@ -579,6 +631,7 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->cg, cg);
   UP(&d->lcs, lcs);
   UP(&d->gjp, gjs);
+  UP(&d->gjpi, gjs_in);
   UP(&d->gp, gps);
   UP(&d->gp128, gps128);
   UP(&d->gpoz, gpsoz);
@@ -748,17 +801,18 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
   // ---- upward (Algorithm 1 first loop, Algorithm 2 fold) ----
   bool tc = false;   // current level's GEMMs on the tensor cores (mixed mode, below the top levels)
   bool schur = false;   // the launch is Algorithm 1's Schur update (profiled separately)
+  bool gjup = false;    // the launch is a Gauss-Jordan trailing update (profiled separately)
   auto gemm = [&](const GemmPair& pr, const GemmArgs& gz, const GemmArgs& gt, const GemmArgs& go) -> int {
     if (gz.total_tiles <= 0) return HSC_OK;
     if (tc && d->PK && d->use_pack)
-      LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 2, gt.flops * ne, 0.0,
+      LAUNCH(gjup ? K_GJU_TC : schur ? K_SCHUR_TC : K_GEMM_TC, 2, gt.flops * ne, 0.0,
              gemm_tc_packed(gt, ne, d->PK, d->pk_cur, d->flag + 2, s));
-    else if (tc) LAUNCH(schur ? K_SCHUR_TC : K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
+    else if (tc) LAUNCH(gjup ? K_GJU_TC : schur ? K_SCHUR_TC : K_GEMM_TC, 1, gt.flops * ne, 0.0, gemm_tc(gt, ne, d->flag + 2, s));
     else if (pr.oz_faster && d->PK && oz_words(go) <= d->pk_cur)
-      LAUNCH(schur ? K_SCHUR_OZ : K_GEMM_OZ, 2, go.flops * ne, 0.0,
+      LAUNCH(gjup ? K_GJU_OZ : schur ? K_SCHUR_OZ : K_GEMM_OZ, 2, go.flops * ne, 0.0,
              gemm_oz(go, ne, reinterpret_cast<uint16_t*>(d->PK), 2 * d->pk_cur,
                      reinterpret_cast<double*>(d->PK + oz_scale_word(go)), d->pk_cur / 2, d->flag + 2, s));
-    else LAUNCH(schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s, d->four_products));
+    else LAUNCH(gjup ? K_GJU : schur ? K_SCHUR : K_GEMM, 1, gz.flops * ne, 0.0, gemm_z(gz, ne, s, d->four_products));
     return HSC_OK;
   };
 #define GEMM(pair, ...)                                                                          \
@@ -786,17 +840,32 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
                               d->dense_es, d->F, d->L, d->aug_es, ne, s));
     // Gauss-Jordan inversion of A_ii in place (D_i^{-1}), panel by panel
     const GJProb* gp = d->gjp + U.gj;
+    const GJProb* gpi = d->gjpi ? d->gjpi + U.gji : nullptr;
     for (size_t st = 0; st < U.steps.size(); ++st) {
-      const int k0 = (int)st * d->nb;
-      LAUNCH(K_GJ_PANEL, 1, 0.0, 0.0,
-             launch_gj_panel(gp, U.nmat, d->F, d->aug_es, d->piv, d->piv_es, d->GJT, d->GJT,
-                             d->gjt_es, k0, d->nb, ne, d->flag, s, d->gj_cluster));
-      LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
-             launch_gj_swap(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
-                            d->gjt_es, k0, d->nb, ne, s));
+      const GjStep& sd = U.sdesc[st];
+      const int k0 = sd.k0;
+      if (sd.kind == 2) {   // the wide panel, reduced by its nested steps: move, swap, product
+        LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
+               launch_gj_move(gp, U.nmat, U.max_n, d->F, d->aug_es, d->GJT, d->GJT, d->gjt_es, k0, d->nbo,
+                              ne, s));
+        LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
+               launch_gj_swap(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
+                              d->gjt_es, k0, d->nbo, ne, s));
+      } else {
+        const GJProb* g = sd.kind == 1 ? gpi : gp;
+        LAUNCH(K_GJ_PANEL, 1, 0.0, 0.0,
+               launch_gj_panel(g, U.nmat, d->F, d->aug_es, d->piv, d->piv_es, d->GJT, d->GJT,
+                               d->gjt_es, k0, d->nb, ne, d->flag, s, d->gj_cluster));
+        LAUNCH(K_GJ_SWAP, 1, 0.0, 0.0,
+               launch_gj_swap(g, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, d->GJT,
+                              d->gjt_es, k0, d->nb, ne, s, sd.kind == 1 ? sd.k1 : 0,
+                              sd.kind == 1 ? sd.k1 + d->nbo : 1 << 30));
+      }
       const bool keep = tc;
       tc = tc && !d->gj_fp64;
+      gjup = true;
       GEMM(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es);
+      gjup = false;
       tc = keep;
     }
     LAUNCH(K_GJ_PERM, 1, 0.0, 0.0,
@@ -909,6 +978,8 @@ int new_state(hsc_ctx* h) {
   h->dev = new DeviceState();
   CK(cudaGetDevice(&h->dev->device));
   h->dev->nb = h->opt_nb;
+  h->dev->nbo = (h->opt_nbo / h->opt_nb) * h->opt_nb;   // a multiple of the panel width
+  if (h->dev->nbo <= h->opt_nb) h->dev->nbo = 0;
   h->dev->fp64_levels = h->opt_fp64_levels;
   h->dev->gj_fp64 = h->opt_gj_fp64 != 0;
   h->dev->four_products = h->opt_4m != 0;

@@ -23,7 +23,8 @@ def _dev_tensor(torch, a):
 
 def test_batch_graph_matches_single_solves(torch):
     """Three cuboids with uneven separators and different energy counts in one graph launch give
-    the same bits as three separate hsc_solve calls; the cached graph replays identically."""
+    the same bits as three separate hsc_solve calls; the cached graph replays identically; every
+    item matches the dense oracle."""
     solvers, items, refs = [], [], []
     for k, d in enumerate(DIMS):
         dev = W.cubic_device(d, W=1.0, seed=1000 + k)
@@ -51,6 +52,20 @@ def test_batch_graph_matches_single_solves(torch):
                 for key, r in zip(("diag_gr", "diag_gl", "req_gr", "req_gl"), ref):
                     got = it[key].cpu().numpy().view(np.complex128)
                     np.testing.assert_array_equal(got, r)
+    # and every item against the dense definition (Eqs. 1-2) at 1e-10
+    for k, (d, it) in enumerate(zip(DIMS, items)):
+        dev = W.cubic_device(d, W=1.0, seed=1000 + k)
+        E = it["E"].cpu().numpy()
+        sr, sl = W.self_energies(dev, len(E))
+        pairs = it["pairs"]
+        Hd = dev.to_scipy().toarray()
+        gr = it["diag_gr"].cpu().numpy().view(np.complex128)
+        gl = it["diag_gl"].cpu().numpy().view(np.complex128)
+        pg = it["req_gr"].cpu().numpy().view(np.complex128)
+        for e in range(len(E)):
+            G, Gl = dense.solve(Hd, E[e], 0.05, dev.contact_unknowns(), sr[e], sl[e])
+            for x, ref in ((gr[e], np.diag(G)), (gl[e], np.diag(Gl)), (pg[e], G[pairs[:, 0], pairs[:, 1]])):
+                assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
     for s in solvers:
         s.close()
 
@@ -89,3 +104,26 @@ def test_panel_width_option_keeps_results(torch, nb):
     s.close()
     for a, b in zip(got[:2], ref[:2]):
         assert np.abs(a - b).max() / np.abs(b).max() <= 1e-12
+
+
+@pytest.mark.parametrize("nb,wide", [(32, 0), (32, 128), (16, 64), (8, 40), (5, 12)])
+def test_nested_gauss_jordan_blocking_against_dense(torch, nb, wide):
+    """Nested blocking of the cluster inversions (HSC_OPT_GJ_WIDE: panels of HSC_OPT_GJ_PANEL width
+    reduced inside a wide panel, then one trailing product with K = the wide width): the same
+    D_i^{-1} as unnested blocking, on leaves of 7 x 8 x 8 = 448 unknowns (a ragged last wide panel
+    for every width) and separators of other sizes; against the dense definition at 1e-10."""
+    dev = W.cubic_device((15, 16, 16), W=1.0, seed=4)
+    E = np.array([-1.7, 0.35])
+    sr, sl = W.self_energies(dev, len(E))
+    s = hsc.Solver(dev, 8)
+    assert hsc.hsc_get_option(s.h, hsc.HSC_OPT_TREE_FORM) == 1
+    hsc.hsc_set_option(s.h, hsc.HSC_OPT_GJ_PANEL, nb)
+    hsc.hsc_set_option(s.h, hsc.HSC_OPT_GJ_WIDE, wide)
+    assert hsc.hsc_get_option(s.h, hsc.HSC_OPT_GJ_WIDE) == wide
+    dgr, dgl, _, _ = s.solve(E, 0.05, sr, sl)
+    s.close()
+    Hd = dev.to_scipy().toarray()
+    for k in range(len(E)):
+        G, Gl = dense.solve(Hd, E[k], 0.05, dev.contact_unknowns(), sr[k], sl[k])
+        assert np.abs(dgr[k] - np.diag(G)).max() / np.abs(np.diag(G)).max() <= 1e-10
+        assert np.abs(dgl[k] - np.diag(Gl)).max() / np.abs(np.diag(Gl)).max() <= 1e-10

@@ -57,7 +57,7 @@ def _dense_case(dev, leaf, energies, eta=ETA_WELL, f=(1.0, 0.0), pairs=None, tol
     dgr, dgl, pgr, pgl = s.solve(energies, eta, sr, sl, pairs=pairs)
     if engine is not None:
         launches = {p["name"]: p["launches"] for p in hsc.hsc_profile_read(s.h)}
-        emulated = launches.get("gemm_z_ozaki", 0) + launches.get("schur_z_ozaki", 0)
+        emulated = sum(launches.get(c, 0) for c in ("gemm_z_ozaki", "schur_z_ozaki", "gj_update_ozaki"))
         # engine 2 runs every product list with K > 0 on the emulation, engine 1 none
         assert (emulated > 0) == (engine == 2), launches
     Hd = dev.to_scipy().toarray()

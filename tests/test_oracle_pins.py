@@ -8,7 +8,9 @@
 * complex symmetry G^r = (G^r)^T and anti-Hermiticity of G^< (the relations used by Algorithms 1-2);
 * Caroli transmission against the lesser-function form, and against |G_1N|^2 Gamma^2 on a chain;
 * RGF against the dense definition on small 3D grids (including several orbitals per site);
-* sparse single-column solves against the dense definition.
+* sparse single-column solves against the dense definition;
+* the density of states of a closed chain against its sum of Lorentzians over the closed-form
+  eigenvalues.
 """
 import numpy as np
 import pytest
@@ -180,3 +182,17 @@ def test_oracle_detects_planted_mistakes():
     Gam[cu] = 0.7
     rhs2 = np.real(np.diag((G2 * Gam) @ G2.conj().T))
     assert np.max(np.abs(-2 * np.imag(np.diag(G2)) - rhs2)) > 1e-3
+
+
+def test_dos_is_the_lorentzian_sum_of_the_closed_chain():
+    """DOS(E) = -(1/pi) sum_n Im G^r_nn of a closed chain (no contacts, hopping t) equals
+    (1/pi) sum_k eta / ((E - e_k)^2 + eta^2) with the closed-form levels e_k = 2 t cos(k pi / (N + 1)):
+    pins observables.dos (sign, 1/pi, imaginary part) independently of any inverse routine."""
+    N, t, eta = 17, -1.0, 0.07
+    H = t * (np.eye(N, k=1) + np.eye(N, k=-1))
+    ek = 2 * t * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    for E in (-1.3, 0.0, 0.55, 1.9):
+        G = dense.retarded(dense.system_matrix(H, E, eta, np.zeros((N, N))))
+        ref = np.sum(eta / ((E - ek) ** 2 + eta ** 2)) / np.pi
+        assert abs(observables.dos(np.diag(G)) - ref) <= 1e-12 * ref
+        assert abs(-np.sum(np.real(np.diag(G))) / np.pi - ref) > 1e-3 * ref   # the real part would not do
