@@ -174,7 +174,7 @@ int hsc_solve_dense(hsc_t h, int64_t n_E, const double* E, double eta, const hsc
  * schedule and workspace (rebuilt by the next solve). HSC_OPT_LEAF is read-only (the leaf_max of
  * the last hsc_analyze). */
 typedef enum {
-  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 32)                   */
+  HSC_OPT_GJ_PANEL = 1,       /* Gauss-Jordan panel width, 1..64 (default 16)                   */
   HSC_OPT_FP64_LEVELS = 2,    /* HSC_MIXED: tree levels from the top kept on the FP64 pipe (2)  */
   HSC_OPT_MIXED_GJ_FP64 = 3,  /* HSC_MIXED: 1 keeps cluster-inverse updates on the FP64 pipe (0) */
   HSC_OPT_LEAF = 4,           /* read only                                                      */
@@ -184,10 +184,11 @@ typedef enum {
   HSC_OPT_FP64_ENGINE = 6,    /* engine of the FP64-accurate block products: 0 (default) picks  */
                               /* per product list by a cost model, 1 = FP64 pipe only, 2 = FP64 */
                               /* emulation on the BF16 tensor cores wherever K > 0. The         */
-                              /* emulation splits each real operand exactly into eight 7-bit    */
-                              /* slices (power-of-two row / column scales) and accumulates the  */
-                              /* slice products exactly; its error per K value is below         */
-                              /* 2^-52.8 times the two scales, at the level of FP64 rounding.   */
+                              /* emulation writes each real operand in eight balanced base-128  */
+                              /* digits (power-of-two row / column scales) and accumulates the  */
+                              /* digit products exactly; its error per K value is below 2^-52.5 */
+                              /* times the row and column maxima' powers of two, at the level   */
+                              /* of FP64 rounding.                                              */
   HSC_OPT_RESOLVE_DIGITS = 7, /* d > 0: hsc_solve solves every energy whose residual (see      */
                               /* hsc_residual; default d = 10: on the 32^3 cube at eta = 1e-6   */
                               /* the default tree leaves 3 of 64 energies above 1e-10, the      */

@@ -29,7 +29,7 @@ struct hsc_ctx {
   std::string err;
   hsc::DeviceState* dev = nullptr;
   // options (hsc_set_option); they survive re-analysis
-  int opt_nb = 32;            // Gauss-Jordan panel width (its trailing updates are GEMMs with K = width)
+  int opt_nb = 16;            // Gauss-Jordan panel width (its trailing updates are GEMMs with K = width)
   int opt_nbo = 128;          // wide panel of the nested blocking (trailing products with K = this)
   int opt_fp64_levels = 2;    // HSC_MIXED: top tree levels kept on the FP64 pipe
   int opt_gj_fp64 = 0;        // HSC_MIXED: Gauss-Jordan trailing updates on the FP64 pipe

@@ -7,21 +7,24 @@
 //     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),
 //     C = beta D + alpha [(1 - i) T0 + (-1 - i) T1 + i T2].
 // Each real product X Y (X: M x K, Y: K x N) is evaluated exactly up to a bounded truncation:
-//   * row i of X gets the power of two sigma_i > max_k |X_ik|, column j of Y likewise tau_j;
-//   * |X_ik| / sigma_i, a number in [0, 1), is truncated to 56 fraction bits and cut into OZ_S = 8
-//     slices of 7 bits; a slice t_s in [-127, 127] (sign of X_ik) is exact in BF16, and
-//         X_ik = sigma_i (sum_s t_s 2^(-7 s) + delta),  |delta| < 2^-56;
-//     the slicing works on the FP64 bit pattern (integer shifts only: GB300's FP64 pipe is slow);
-//   * a slice product t_s u_r is an integer below 2^14 and carries the weight 2^(-7 (s + r)); the
+//   * row i of X gets the power of two sigma_i > 2 max_k |X_ik|, column j of Y likewise tau_j;
+//   * X_ik / sigma_i, a number in (-1/2, 1/2), is truncated towards zero to 56 fraction bits and
+//     written in balanced base-128 digits: X_ik = sigma_i (sum_s t_s 2^(-7 s) + delta), |delta| <
+//     2^-56, with OZ_S = 8 digits t_s in [-64, 63] (the leading one in [-65, 65]), each exact in
+//     BF16; the slicing works on the FP64 bit pattern (integer operations only: GB300's FP64 pipe is
+//     slow);
+//   * a digit product t_s u_r has |t_s u_r| <= 65^2 and carries the weight 2^(-7 (s + r)); the
 //     products of one diagonal d = s + r (d <= OZ_S + 1: 36 pairs) accumulate in one FP32 tensor-
-//     memory accumulator, exact for 128 K values (at most 8 pairs: 8 * 127^2 * 128 < 2^24); every
-//     128 K values the 8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe
-//     would otherwise bound the kernel), into the 96-bit integer T 2^63 = H 2^32 + L per element
-//     (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)); once per product T sigma_i
-//     tau_j is rounded to the nearest double, also on the integer pipe (the scales are powers of
-//     two), the only rounding;
-//   * per K value the error is below 2^-52.8 sigma_i tau_j: 2 * 2^-56 from the truncation and
-//     2^-53.1 from the dropped diagonals d >= 10 (7 * 127^2 * 2^-70 for d = 10, less beyond).
+//     memory accumulator, exact for 384 K values (at most 8 pairs: 8 * 65^2 * 384 < 2^24; the
+//     balanced digits give four times the headroom of digits in [0, 127]); every 384 K values the
+//     8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe would otherwise
+//     bound the kernel), into the 96-bit integer T 2^63 = H 2^32 + L per element (int64 H,
+//     uint32 L; diagonal d carries the weight 2^(49 - 7 d)); once per product T sigma_i tau_j is
+//     rounded to the nearest double, also on the integer pipe (the scales are powers of two), the
+//     only rounding;
+//   * per K value the error is below 2^-54.5 sigma_i tau_j (2^-52.5 times the products of the row
+//     and column maxima' powers of two): 2^-56 from the truncations (|X_ik| < sigma_i / 2) and
+//     2^-55.2 from the dropped diagonals d >= 10 (7 * 64^2 * 2^-70 for d = 10, less beyond).
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
 // op(A) (all 8 slices, 32 KB) and a 64 x 16 block of op(B)^T (16 KB) in the K-major core-matrix
 // layout the MMA reads, for each of the three real operands (re, im, re + im), reading each complex
@@ -29,7 +32,7 @@
 // Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
 // real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
 // counts), warp 1 issues the 36 MMAs of each K step into the 8 diagonal accumulators (512 TMEM
-// columns), warps 2-17 drain them every 8 K steps (16 columns of exact state per thread)
+// columns), warps 2-17 drain them every 24 K steps (16 columns of exact state per thread)
 // and, after the last chunk of a real product, add its share to C (read-modify-write by the owning
 // thread, so C may alias D). Every mbarrier wait is bounded; on expiry the kernel raises the flag,
 // waits (bounded) for its own copies, frees tensor memory and returns.
@@ -50,7 +53,8 @@ constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;
 constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (all slices)
 constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
 constexpr int OZ_STAGES = 4;
-constexpr int OZ_DRAIN = 8;              // K steps per drain (128 K values)
+constexpr int OZ_DRAIN = 24;             // K steps per drain (384 K values)
+constexpr int OZ_TMAX = 65;              // largest |digit|
 constexpr int OZ_ACC = OZ_ND * OZ_BN;     // TMEM columns of one set of accumulators
 constexpr uint32_t OZ_TMEM_COLS = 512;
 constexpr int OZ_NBUF = 2 * OZ_ACC <= (int)OZ_TMEM_COLS ? 2 : 1;   // sets (2: drain overlaps MMAs)
@@ -61,7 +65,7 @@ constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;
 constexpr int OZP_THREADS = 256;
 
 static_assert(OZ_NBUF * OZ_ACC <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
-static_assert((long long)OZ_S * 127 * 127 * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
+static_assert((long long)OZ_S * OZ_TMAX * OZ_TMAX * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
 static_assert(OZ_ND == 8 && OZ_BITS == 7, "the drain's diagonal weights assume 8 diagonals of 7 bits");
 
 __device__ __forceinline__ uint32_t oz_su32(const void* p) {
@@ -209,10 +213,10 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
     if (e2) atomicMax(&s_e[2][r], e2);
   }
   __syncthreads();
-  // sigma = 2^(E - 1022) > |x| for every x of the row with biased exponent <= E
+  // sigma = 2^(E - 1021) > 2 |x| for every x of the row with biased exponent <= E
   for (int i = tid; i < 3 * rows; i += OZP_THREADS) {
     const int v = i / rows, r = i % rows;
-    sc[v * sstride + r] = s_e[v][r] > 0 ? ldexp(1.0, s_e[v][r] - 1022) : 0.0;
+    sc[v * sstride + r] = s_e[v][r] > 0 ? ldexp(1.0, s_e[v][r] - 1021) : 0.0;
   }
   // pass 2: slices, 8 consecutive k of one row per task
   for (int t = tid; t < ntask; t += OZP_THREADS) {
@@ -223,29 +227,41 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
     uint16_t* o = dst + (int64_t)(k0 / OZ_BK) * blkv + oz_cidx(r, k0 % OZ_BK);
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      unsigned long long m[8];
-      uint32_t sg[8];
+      long long m[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const double val = v == 0 ? x[q].x : (v == 1 ? x[q].y : x[q].x + x[q].y);
         const unsigned long long bits = (unsigned long long)__double_as_longlong(val);
         const int ex = (int)((bits >> 52) & 0x7FF);
-        // m = floor(|x| / sigma * 2^56): |x| = mant 2^(ex - 1075), sigma = 2^(E - 1022), so the 53-bit
-        // significand moves right by E - ex + 52 - 56 + 1 (a left shift of at most 3 when ex = E)
-        const int shift = s_e[v][r] - ex + (52 - OZ_FRAC + 1);
+        // floor(|x| / sigma * 2^56) < 2^55: |x| = mant 2^(ex - 1075), sigma = 2^(E - 1021), so the
+        // 53-bit significand moves right by E - ex + 52 - 56 + 2 (a left shift of at most 2)
+        const int shift = s_e[v][r] - ex + (52 - OZ_FRAC + 2);
         const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        m[q] = (ex > 0 && shift < 64) ? (shift >= 0 ? mant >> shift : mant << (-shift)) : 0ull;
-        sg[q] = (uint32_t)(bits >> 63) << 15;
+        const long long mag = (ex > 0 && shift < 64) ? (long long)(shift >= 0 ? mant >> shift : mant << (-shift)) : 0ll;
+        m[q] = (bits >> 63) ? -mag : mag;
       }
+      // balanced base-128 digits, least significant first: t = ((m + 64) mod 128) - 64, m = (m - t) / 128
+      int dg[OZ_S][8];
+#pragma unroll
+      for (int sl = OZ_S - 1; sl > 0; --sl)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int t = (int)((m[q] + 64) & 127) - 64;
+          dg[sl][q] = t;
+          m[q] = (m[q] - t) >> 7;   // exact: m - t is a multiple of 128
+        }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dg[0][q] = (int)m[q];   // the leading digit, |t| <= 65
 #pragma unroll
       for (int sl = 0; sl < OZ_S; ++sl) {
         uint32_t h[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const uint32_t tq = (uint32_t)(m[q] >> (OZ_FRAC - OZ_BITS * (sl + 1))) & 127u;
-          // tq as an FP32 value (exact: tq < 2^23), whose upper half is its exact BF16 encoding
+          const int t = dg[sl][q];
+          const uint32_t tq = (uint32_t)(t < 0 ? -t : t);
+          // |t| as an FP32 value (exact: |t| < 2^23), whose upper half is its exact BF16 encoding
           const float f = __uint_as_float(0x4B000000u | tq) - 8388608.0f;
-          h[q] = (__float_as_uint(f) >> 16) | sg[q];
+          h[q] = (__float_as_uint(f) >> 16) | (t < 0 ? 0x8000u : 0u);
         }
         uint4 w;
         w.x = h[0] | (h[1] << 16);

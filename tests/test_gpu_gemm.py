@@ -90,8 +90,8 @@ def test_tcgen05_3xtf32_engine(lib, oa, ob, M, N, K):
 @pytest.mark.parametrize("oa,ob", OPS)
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_fp64_emulation_engine(lib, oa, ob, M, N, K):
-    """Eight slices of 7 bits on the BF16 tensor cores: per K value the error is below
-    2^-52.8 sigma tau (power-of-two row and column scales), so at FP64 level of |A||B|."""
+    """Eight balanced base-128 digits on the BF16 tensor cores: per K value the error is below
+    2^-52.5 times the row and column maxima's powers of two, so at FP64 level of |A||B|."""
     err = run(lib, 4, oa, ob, M, N, K, M + N + K)
     assert err <= 1e-13, err
 
@@ -121,27 +121,46 @@ def test_fp64_emulation_exact_on_short_integers(lib, K):
     assert np.array_equal(C, A @ B)
 
 
-@pytest.mark.parametrize("K", [128, 200, 1000])
-def test_fp64_emulation_full_slices(lib, K):
-    """x = 1 - 2^-53 (the largest double below 1) makes slices 1-7 equal to 127 and slice 8 equal to
-    120: the largest FP32 partial sums the accumulation meets (8 pairs on diagonal 9, 16.3e6 over
-    128 K values, below 2^24). The result must be K times the kept diagonals (s + r <= 9) up to the
-    FP64 rounding of the drain; a lost unit in the accumulator of diagonal d would add
-    2^(-7 d) per chunk."""
+@pytest.mark.parametrize("K", [200, 384, 1000])
+def test_fp64_emulation_full_digits(lib, K):
+    """x = sum_s d_s 2^(-7 s) with balanced base-128 digits d = (63, ..., 63, 60) (53 significant
+    bits, in [1/4, 1/2), so its row scale is 1): every digit product on diagonal 9 is ~63^2 and the
+    FP32 accumulators meet their largest partial sums (8 pairs, 12.2e6 over 384 K values, below
+    2^24). The result must be K times the kept diagonals (s + r <= 9) up to the FP64 rounding of
+    the drain; a lost unit in the accumulator of diagonal d would add 2^(-7 d) per chunk."""
     from fractions import Fraction
-    x = 1.0 - 2.0 ** -53
-    t = [127] * 7 + [120]
-    assert sum(Fraction(t[s - 1], 2 ** (7 * s)) for s in range(1, 9)) == Fraction(x)
+    t = [63] * 7 + [60]
+    xf = sum(Fraction(t[s - 1], 2 ** (7 * s)) for s in range(1, 9))
+    x = float(xf)
+    assert Fraction(x) == xf and 0.25 <= x < 0.5
     pairs = [(s, r) for s in range(1, 9) for r in range(1, 9)]
     term = lambda s, r: Fraction(t[s - 1] * t[r - 1], 2 ** (7 * (s + r)))
     kept = sum(term(s, r) for s, r in pairs if s + r <= 9)
-    dropped = sum(term(s, r) for s, r in pairs if s + r >= 10)
-    assert kept + dropped == Fraction(x) ** 2
+    assert kept + sum(term(s, r) for s, r in pairs if s + r >= 10) == xf ** 2
+    assert sum(t[s - 1] * t[8 - s] for s in range(1, 9)) * 384 < 2 ** 24   # diagonal 9, one chunk
     A = np.full((130, K), x, dtype=np.complex128)
     B = np.full((K, 70), x, dtype=np.complex128)
     C = _emulated(lib, A, B)
     assert np.all(C.imag == 0.0)
     assert np.max(np.abs(C.real - float(K * kept))) <= K * 2.0 ** -50
+
+
+def test_fp64_emulation_within_row_dynamic_range(lib):
+    """Entries of one row of A (and of one column of B) spanning 2^-40 .. 1: the emulation keeps 56
+    bits relative to each row's and column's largest power of two, so its error obeys
+    |C - AB| <= K 2^-52.5 rowmax(|A|) colmax(|B|) (the documented bound; a componentwise
+    K u |A||B| bound does not hold for entries far below their row's maximum, which keep fewer
+    bits)."""
+    rng = np.random.default_rng(11)
+    M, N, K = 96, 80, 700
+    mag = lambda *sh: 2.0 ** rng.uniform(-40, 0, sh)
+    A = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * mag(M, K)
+    B = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * mag(K, N)
+    C = _emulated(lib, A, B)
+    ref = A @ B
+    pw = lambda a, ax: 2.0 ** np.ceil(np.log2(np.max(np.abs(a), axis=ax)))
+    bound = 16 * K * pw(A, 1)[:, None] * pw(B, 0)[None, :] * 2.0 ** -52.5   # 3 real products, scales <= 4 pw
+    assert np.all(np.abs(C - ref) <= bound)
 
 
 def test_fp64_emulation_row_scaling(lib):
