@@ -90,8 +90,11 @@ def test_resonant_interior_block_on_the_plain_tree_and_the_default_tree():
     """At E = 0 the 7x5x6 grid (seed 18, leaves <= 2) has, on the plain geometric tree, a 4-site
     interior leaf whose local level sits within ~1e-4 of E; its block carries only eta, so no FP64
     evaluation of Algorithm 1 over that tree reaches 1e-10 (a LAPACK evaluation of the same block
-    steps is off by 2.4e-7): the GPU result is bounded by its residual and by TOL_RESONANT. On the
-    default contact-connected tree every block holds contact sites and the result meets TOL."""
+    steps is off by 2.4e-7): the GPU result is bounded by TOL_RESONANT. With leaves of a few sites
+    the residual does not bound it: the amplified rounding lies along the level's vector, which A
+    nearly annihilates (measured: error 1.3e-7 at residual 1.5e-10). On the default
+    contact-connected tree every block holds contact sites and the result meets TOL, with the
+    residual at rounding level."""
     dev = W.cubic_device((7, 5, 6), W=1.0, seed=18)
     sr, sl = W.self_energies(dev, 1, (1.0, 0.3))
     G, Gl = dense.solve(dev.to_scipy().toarray(), 0.0, 1e-6, dev.contact_unknowns(), sr[0], sl[0])
@@ -102,7 +105,9 @@ def test_resonant_interior_block_on_the_plain_tree_and_the_default_tree():
         s.close()
         err = max(relerr(dgr[0], np.diag(G)), relerr(dgl[0], np.diag(Gl)))
         print(f"7x5x6 E=0 ordering {ordering}: error {err:.2e}, residual {res:.1e}")
-        assert err <= tol and relerr(dgr[0], np.diag(G)) <= RES_FACTOR * res + 1e-13
+        assert err <= tol
+        if ordering == 0:
+            assert relerr(dgr[0], np.diag(G)) <= RES_FACTOR * res + 1e-13
 
 
 def test_multi_orbital_wire():
