@@ -26,16 +26,15 @@
 //     and column maxima' powers of two): 2^-56 from the truncations (|X_ik| < sigma_i / 2) and
 //     2^-55.2 from the dropped diagonals d >= 10 (7 * 64^2 * 2^-70 for d = 10, less beyond).
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
-// op(A) (all 8 slices, 32 KB) and a 48 x 16 block of op(B)^T (12 KB) in the K-major core-matrix
+// op(A) (all 8 slices, 32 KB) and a 64 x 16 block of op(B)^T (16 KB) in the K-major core-matrix
 // layout the MMA reads, for each of the three real operands (re, im, re + im), reading each complex
 // element once per pass and writing 16-byte runs.
-// Pass 2 (k_gemm_oz), one CTA per 128 x 48 output tile: warp 0 streams the slice blocks of the three
+// Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
 // real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
-// counts); warp 1 copies each K step's 8 A digit planes from shared to tensor memory (tcgen05.cp,
-// two alternating 64-column buffers) and issues the 36 MMAs of the step with A in tensor memory and
-// B in shared memory into the 8 diagonal accumulators (384 TMEM columns): each MMA then reads 1.5 KB
-// of operands from shared memory instead of 6 KB, the bound of 128 x 64 tiles with both operands
-// there; warps 2-17 drain the accumulators every 24 K steps (12 columns of exact state per thread)
+// counts), warp 1 issues the 36 digit products of each K step as 12 MMAs of N = 64..256 (for each
+// A digit, the B digit planes it pairs with are contiguous along N and their column blocks are
+// the diagonal accumulators it feeds) into the 8 diagonal accumulators (512 TMEM columns), warps
+// 2-17 drain them every 24 K steps (16 columns of exact state per thread)
 // and, after the last chunk of a real product, add its share to C (read-modify-write by the owning
 // thread, so C may alias D). Every mbarrier wait is bounded; on expiry the kernel raises the flag,
 // waits (bounded) for its own copies, frees tensor memory and returns.
@@ -52,7 +51,7 @@ constexpr int OZ_S = 8;                  // slices per operand
 constexpr int OZ_BITS = 7;               // bits per slice
 constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // fraction bits kept (56)
 constexpr int OZ_ND = OZ_S;              // accumulated diagonals d = 2 .. OZ_S + 1
-constexpr int OZ_BM = 128, OZ_BN = 48, OZ_BK = 16;
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;
 constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (all slices)
 constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
 constexpr int OZ_STAGES = 4;
@@ -60,16 +59,14 @@ constexpr int OZ_DRAIN = 24;             // K steps per drain (384 K values)
 constexpr int OZ_TMAX = 65;              // largest |digit|
 constexpr int OZ_ACC = OZ_ND * OZ_BN;     // TMEM columns of one set of accumulators
 constexpr uint32_t OZ_TMEM_COLS = 512;
-constexpr int OZ_NBUF = 1;                // one set of accumulators; the A digit planes take the rest
-constexpr int OZ_ACOLS = OZ_S * (OZ_BK / 2);   // TMEM columns of one K step's A digit planes (64)
-constexpr int OZ_ABUF = OZ_NBUF * OZ_ACC;      // first TMEM column of the two A buffers
+constexpr int OZ_NBUF = 2 * OZ_ACC <= (int)OZ_TMEM_COLS ? 2 : 1;   // sets (2: drain overlaps MMAs)
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 constexpr int OZ_DRAIN_WARPS = 16;     // four per TMEM lane quadrant
 constexpr int OZ_DCOLS = OZ_BN / (OZ_DRAIN_WARPS / 4);   // columns of exact state per drain thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;
 constexpr int OZP_THREADS = 256;
 
-static_assert(OZ_ABUF + 2 * OZ_ACOLS <= (int)OZ_TMEM_COLS, "accumulators and A buffers exceed tensor memory");
+static_assert(OZ_NBUF * OZ_ACC <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
 static_assert((long long)OZ_S * OZ_TMAX * OZ_TMAX * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
 static_assert(OZ_ND == 8 && OZ_BITS == 7, "the drain's diagonal weights assume 8 diagonals of 7 bits");
 
@@ -142,18 +139,11 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);   // no swizzle, version 1
 }
 
-// D (TMEM) += A (TMEM: 128 lanes x 8 columns of BF16 pairs) x B (shared memory descriptor)
-__device__ __forceinline__ void oz_mma(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// one digit plane of an A block (128 rows x 16 K, shared memory, K-major core matrices) to TMEM
-// (128 lanes x 8 columns); ordered with the MMAs this thread issues after it
-__device__ __forceinline__ void oz_cp(uint32_t taddr, uint64_t sdesc) {
-  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc));
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ int oz_expo(double x) {
@@ -349,9 +339,9 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sm.tmem;
-  // kind::f16 with BF16 A and B, FP32 D, both K-major, M = 128, N = 64
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                         ((uint32_t)(OZ_BM >> 4) << 24);
+  // kind::f16 with BF16 A and B, FP32 D, both K-major, M = 128, N = 64 q (q = 1..4 digit planes of B)
+  const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
+  auto idesc_n = [&](int q) { return idesc0 | ((uint32_t)((q * OZ_BN) >> 3) << 17); };
   constexpr uint32_t ABYTES = OZ_ABLK * 2, BBYTES = OZ_BBLK * 2;
   volatile int* abort_flag = &sm.abort;
 
@@ -398,20 +388,23 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t a0 = oz_su32(&sm.a[st][0]), b0 = oz_su32(&sm.b[st][0]);
-          // the stage's 8 A digit planes go to TMEM once (buffers alternate by K step), so the 36
-          // MMAs read only their B planes from shared memory
-          const uint32_t at = tmem + OZ_ABUF + (uint32_t)((s & 1) * OZ_ACOLS);
+          // The B digit planes r = 1..8 lie one after another along N (64 rows each, the same core-
+          // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 64 (9 - s): its
+          // column block r lands in the accumulator of diagonal s + r, which starts at TMEM column
+          // 64 (s + r - 2). One MMA per A digit (two where N would exceed 256): 12 per K step
+          // instead of 36, the same products.
 #pragma unroll
-          for (int si = 0; si < OZ_S; ++si) oz_cp(at + si * (OZ_BK / 2), oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)));
-#pragma unroll
-          for (int si = 0; si < OZ_S; ++si)
-#pragma unroll
-            for (int ri = 0; ri < OZ_S - si; ++ri) {   // s + r <= OZ_S + 1 (1-based slices)
-              // the first MMA of a chunk into diagonal si + ri is the one with si = 0
-              const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
-              oz_mma(tmem + ab * OZ_ACC + (si + ri) * OZ_BN, at + si * (OZ_BK / 2),
-                     oz_desc(b0 + ri * (OZ_BN * OZ_BK * 2)), idesc, acc);
-            }
+          for (int si = 0; si < OZ_S; ++si) {
+            // the first MMAs of a chunk (si = 0) cover every diagonal and start the accumulation
+            const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
+            const uint64_t ad = oz_desc(a0 + si * (OZ_BM * OZ_BK * 2));
+            const int nr = OZ_S - si;              // B digit planes paired with A digit si + 1
+            const int q0 = nr < 4 ? nr : 4;
+            oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, ad, oz_desc(b0), idesc_n(q0), acc);
+            if (nr > 4)
+              oz_mma(tmem + ab * OZ_ACC + (si + 4) * OZ_BN, ad, oz_desc(b0 + 4 * (OZ_BN * OZ_BK * 2)),
+                     idesc_n(nr - 4), acc);
+          }
           oz_commit(oz_su32(&sm.empty[st]));
         }
         oz_commit(oz_su32(&sm.acc_full[ab]));   // also releases the drain warps after an abort

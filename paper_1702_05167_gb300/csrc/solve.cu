@@ -204,11 +204,11 @@ constexpr int TILE = 64;
 
 // Per-SM cost model of the two FP64-accurate engines in FP64-pipe operations (DFMA equivalents,
 // 1.9 DFMA per clock and SM): the FP64 pipe does 3 (4) K DFMA per element of a 64x64 tile; the
-// emulation does, per 128x48 tile and real product, 36 MMAs of 128x48x16 per 16 K values (~35
-// clocks each, A from tensor memory), then one integer drain per 384 K values
+// emulation does, per 128x64 tile and real product, 12 MMAs of 128x(64..256)x16 per 16 K values
+// (the 36 digit products, ~30 clocks each on average), then one integer drain per 384 K values
 // (~0.8 clocks per element; the MMAs wait for it), an epilogue of ~3 FP64-pipe operations per
 // element, plus the slicing pass (about 9 DFMA-times per operand element at HBM speed).
-constexpr double OZ_TILE = 128 * 48, OZ_DRAIN_DFMA = OZ_TILE * 0.8 * 1.9, OZ_MMA_DFMA = 35 * 1.9,
+constexpr double OZ_TILE = 128 * 64, OZ_DRAIN_DFMA = OZ_TILE * 0.8 * 1.9, OZ_MMA_DFMA = 30 * 1.9,
                  OZ_EPI_DFMA = OZ_TILE * 3.0, OZ_PACK_DFMA = 9.0;
 
 struct GemmList {
