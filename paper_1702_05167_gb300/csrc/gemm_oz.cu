@@ -40,6 +40,7 @@
 // waits (bounded) for its own copies, frees tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -297,26 +298,42 @@ __device__ __forceinline__ void oz_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
 }
 
+// Persistent: each CTA takes the items (energy, output tile) idx = blockIdx.x, blockIdx.x + gridDim.x,
+// ... in turn, with its stage ring, accumulator hand-off and barrier phases running on across items.
+// The producer therefore streams the next item's slice blocks while the drain warps finish the
+// current one, and the next item's MMAs start as soon as the accumulators are read, overlapping the
+// current item's epilogue (read-modify-write of C).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* scales, int64_t scale_es,
-          int* flag) {
+          int* flag, int n_items) {
   extern __shared__ unsigned char smem_raw[];
   OzSmem& sm = *reinterpret_cast<OzSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int e = blockIdx.y;
-  int lo = 0, hi = g.nprob - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (g.probs[mid].tile_start <= (int)blockIdx.x) lo = mid;
-    else hi = mid - 1;
-  }
-  const GemmProb P = g.probs[lo];
-  const int t = blockIdx.x - P.tile_start;
-  const int tm = t / P.tiles_n, tn = t % P.tiles_n;
-  const int ks = P.ksteps;
-  const int nchunk = (ks + OZ_DRAIN - 1) / OZ_DRAIN;   // per real product
-  const uint16_t* sl = slices + e * slice_es;
+  // item idx: energy idx / total_tiles, tile idx % total_tiles of problem P (binary search on the
+  // problems' first tiles)
+  struct Item {
+    GemmProb P;
+    int e, tm, tn, ks, nchunk;
+  };
+  auto item = [&](int idx) {
+    Item it;
+    it.e = idx / g.total_tiles;
+    const int tile = idx - it.e * g.total_tiles;
+    int lo = 0, hi = g.nprob - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (g.probs[mid].tile_start <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    it.P = g.probs[lo];
+    const int t = tile - it.P.tile_start;
+    it.tm = t / it.P.tiles_n;
+    it.tn = t % it.P.tiles_n;
+    it.ks = it.P.ksteps;
+    it.nchunk = (it.ks + OZ_DRAIN - 1) / OZ_DRAIN;   // per real product
+    return it;
+  };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_su32(&sm.tmem)),
@@ -346,167 +363,189 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
   volatile int* abort_flag = &sm.abort;
 
   if (warp == 0) {
-    if (lane == 0) {   // producer: the K steps of the three real products in sequence
-      const int nsteps = 3 * ks;
-      for (int s = 0; s < nsteps; ++s) {
-        const int st = s % OZ_STAGES;
-        if (s >= OZ_STAGES && !oz_wait(oz_su32(&sm.empty[st]), (uint32_t)((s / OZ_STAGES - 1) & 1))) {
-          atomicExch(flag, 3);
-          *abort_flag = 1;
-          break;
+    if (lane == 0) {   // producer: per item, the K steps of the three real products in sequence
+      int sg = 0;      // stages issued so far (all items)
+      bool ok = true;
+      for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+        const Item it = item(idx);
+        const uint16_t* sl = slices + it.e * slice_es;
+        for (int s = 0; s < 3 * it.ks; ++s, ++sg) {
+          const int st = sg % OZ_STAGES;
+          if (sg >= OZ_STAGES && !oz_wait(oz_su32(&sm.empty[st]), (uint32_t)((sg / OZ_STAGES - 1) & 1))) {
+            atomicExch(flag, 3);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const int v = s / it.ks, kk = s % it.ks;
+          const uint16_t* pa = sl + it.P.pa + (((int64_t)v * it.P.tiles_m + it.tm) * it.ks + kk) * OZ_ABLK;
+          const uint16_t* pb = sl + it.P.pb + (((int64_t)v * it.P.tiles_n + it.tn) * it.ks + kk) * OZ_BBLK;
+          const uint32_t fb = oz_su32(&sm.full[st]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ABYTES + BBYTES)
+                       : "memory");
+          oz_bulk(oz_su32(&sm.a[st][0]), pa, ABYTES, fb);
+          oz_bulk(oz_su32(&sm.b[st][0]), pb, BBYTES, fb);
         }
-        const int v = s / ks, kk = s % ks;
-        const uint16_t* pa = sl + P.pa + (((int64_t)v * P.tiles_m + tm) * ks + kk) * OZ_ABLK;
-        const uint16_t* pb = sl + P.pb + (((int64_t)v * P.tiles_n + tn) * ks + kk) * OZ_BBLK;
-        const uint32_t fb = oz_su32(&sm.full[st]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ABYTES + BBYTES)
-                     : "memory");
-        oz_bulk(oz_su32(&sm.a[st][0]), pa, ABYTES, fb);
-        oz_bulk(oz_su32(&sm.b[st][0]), pb, BBYTES, fb);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
+      int sg = 0, cg = 0;   // stages consumed, chunks issued (all items)
       bool ok = true;
-      for (int c = 0; c < 3 * nchunk && ok; ++c) {
-        const int ab = c % OZ_NBUF;   // accumulator set of this chunk; its previous chunk was c - OZ_NBUF
-        if (c >= OZ_NBUF && !oz_wait(oz_su32(&sm.acc_empty[ab]), (uint32_t)((c / OZ_NBUF - 1) & 1))) {
-          atomicExch(flag, 3);
-          *abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const int v = c / nchunk, cc = c % nchunk;
-        const int s0 = v * ks + cc * OZ_DRAIN, s1 = v * ks + min(ks, (cc + 1) * OZ_DRAIN);
-        for (int s = s0; s < s1; ++s) {
-          const int st = s % OZ_STAGES;
-          if (!oz_wait(oz_su32(&sm.full[st]), (uint32_t)((s / OZ_STAGES) & 1))) {
+      for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+        const Item it = item(idx);
+        for (int c = 0; c < 3 * it.nchunk && ok; ++c, ++cg) {
+          const int ab = cg % OZ_NBUF;   // accumulator set of this chunk; its previous use was cg - OZ_NBUF
+          if (cg >= OZ_NBUF && !oz_wait(oz_su32(&sm.acc_empty[ab]), (uint32_t)((cg / OZ_NBUF - 1) & 1))) {
             atomicExch(flag, 3);
             *abort_flag = 1;
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a0 = oz_su32(&sm.a[st][0]), b0 = oz_su32(&sm.b[st][0]);
-          // The B digit planes r = 1..8 lie one after another along N (64 rows each, the same core-
-          // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 64 (9 - s): its
-          // column block r lands in the accumulator of diagonal s + r, which starts at TMEM column
-          // 64 (s + r - 2). One MMA per A digit (two where N would exceed 256): 12 per K step
-          // instead of 36, the same products.
+          const int v = c / it.nchunk, cc = c % it.nchunk;
+          const int s0 = v * it.ks + cc * OZ_DRAIN, s1 = v * it.ks + min(it.ks, (cc + 1) * OZ_DRAIN);
+          for (int s = s0; s < s1; ++s, ++sg) {
+            const int st = sg % OZ_STAGES;
+            if (!oz_wait(oz_su32(&sm.full[st]), (uint32_t)((sg / OZ_STAGES) & 1))) {
+              atomicExch(flag, 3);
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = oz_su32(&sm.a[st][0]), b0 = oz_su32(&sm.b[st][0]);
+            // The B digit planes r = 1..8 lie one after another along N (64 rows each, the same core-
+            // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 64 (9 - s): its
+            // column block r lands in the accumulator of diagonal s + r, which starts at TMEM column
+            // 64 (s + r - 2). One MMA per A digit (two where N would exceed 256): 12 per K step
+            // instead of 36, the same products.
 #pragma unroll
-          for (int si = 0; si < OZ_S; ++si) {
-            // the first MMAs of a chunk (si = 0) cover every diagonal and start the accumulation
-            const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
-            const uint64_t ad = oz_desc(a0 + si * (OZ_BM * OZ_BK * 2));
-            const int nr = OZ_S - si;              // B digit planes paired with A digit si + 1
-            const int q0 = nr < 4 ? nr : 4;
-            oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, ad, oz_desc(b0), idesc_n(q0), acc);
-            if (nr > 4)
-              oz_mma(tmem + ab * OZ_ACC + (si + 4) * OZ_BN, ad, oz_desc(b0 + 4 * (OZ_BN * OZ_BK * 2)),
-                     idesc_n(nr - 4), acc);
+            for (int si = 0; si < OZ_S; ++si) {
+              // the first MMAs of a chunk (si = 0) cover every diagonal and start the accumulation
+              const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
+              const uint64_t ad = oz_desc(a0 + si * (OZ_BM * OZ_BK * 2));
+              const int nr = OZ_S - si;              // B digit planes paired with A digit si + 1
+              const int q0 = nr < 4 ? nr : 4;
+              oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, ad, oz_desc(b0), idesc_n(q0), acc);
+              if (nr > 4)
+                oz_mma(tmem + ab * OZ_ACC + (si + 4) * OZ_BN, ad, oz_desc(b0 + 4 * (OZ_BN * OZ_BK * 2)),
+                       idesc_n(nr - 4), acc);
+            }
+            oz_commit(oz_su32(&sm.empty[st]));
           }
-          oz_commit(oz_su32(&sm.empty[st]));
+          oz_commit(oz_su32(&sm.acc_full[ab]));   // also releases the drain warps after an abort
         }
-        oz_commit(oz_su32(&sm.acc_full[ab]));   // also releases the drain warps after an abort
       }
     }
   } else {   // warps 2..: drain, TMEM lane quadrant = warp % 4, column part = (warp - 2) / 4
     const int quad = warp & 3, part = (warp - 2) >> 2;
-    const int row = tm * OZ_BM + quad * 32 + lane;
-    c64* C = reinterpret_cast<c64*>(g.C) + e * g.c_es + P.c;
-    const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
-    const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
-    const int col0 = tn * OZ_BN + part * OZ_DCOLS;
-    // exact running sum T 2^63 = H 2^32 + L of the chunks; |H| < nchunk 2^41.1, exact in FP64 for
-    // nchunk < 2^11 (K < 262144)
-    long long H[OZ_DCOLS];
-    unsigned int L[OZ_DCOLS];
+    int cg = 0;   // chunks drained (all items)
+    bool ok = true;
+    for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+      const Item it = item(idx);
+      const GemmProb& P = it.P;
+      const int e = it.e;
+      const int row = it.tm * OZ_BM + quad * 32 + lane;
+      c64* C = reinterpret_cast<c64*>(g.C) + e * g.c_es + P.c;
+      const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
+      const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
+      const int col0 = it.tn * OZ_BN + part * OZ_DCOLS;
+      // exact running sum T 2^63 = H 2^32 + L of the chunks; |H| < nchunk 2^41.6, exact in FP64 for
+      // nchunk < 2^11 (K < 786432)
+      long long H[OZ_DCOLS];
+      unsigned int L[OZ_DCOLS];
 #pragma unroll
-    for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
-    if (ks == 0 && row < P.M) {   // C = beta D
-      for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
-        c64 o = make_double2(0.0, 0.0);
-        if (use_d) {
-          const c64 dv = D[(int64_t)row * P.ldd + col0 + j];
-          o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
-        }
-        C[(int64_t)row * P.ldc + col0 + j] = o;
-      }
-    }
-    for (int c = 0; c < 3 * nchunk; ++c) {
-      const int ab = c % OZ_NBUF;
-      bool got = oz_wait(oz_su32(&sm.acc_full[ab]), (uint32_t)((c / OZ_NBUF) & 1));
-      got = __all_sync(0xffffffffu, got);   // warp-uniform before the .sync.aligned TMEM loads
-      if (!got) {
-        if (lane == 0) atomicExch(flag, 3);
-        break;
-      }
-      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-      for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
-        // all 8 diagonals of 2 columns behind one wait
-        uint32_t r[OZ_ND][2];
-        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ab * OZ_ACC + part * OZ_DCOLS + c0;
-#pragma unroll
-        for (int dg = 0; dg < OZ_ND; ++dg)
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-                       : "=r"(r[dg][0]), "=r"(r[dg][1])
-                       : "r"(ta + dg * OZ_BN));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)); d >= 3 in
-          // b = sum v_d 2^(49 - 7 d) < 2^52.1, added to (H, L) with the carry out of the low word
-          long long x[OZ_ND];
-#pragma unroll
-          for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
-          const long long b = x[3] * (1ll << 28) + x[4] * (1ll << 21) + x[5] * (1ll << 14) + x[6] * (1ll << 7) + x[7];
-          const unsigned int lw = (unsigned int)b;
-          const unsigned int ln = L[c0 + j] + lw;
-          H[c0 + j] += x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32) + (ln < lw ? 1 : 0);
-          L[c0 + j] = ln;
+      for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
+      if (it.ks == 0 && row < P.M) {   // C = beta D
+        for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
+          c64 o = make_double2(0.0, 0.0);
+          if (use_d) {
+            const c64 dv = D[(int64_t)row * P.ldd + col0 + j];
+            o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
+          }
+          C[(int64_t)row * P.ldc + col0 + j] = o;
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty[ab])) : "memory");
-      const int v = c / nchunk;
-      if (c % nchunk == nchunk - 1) {   // real product v complete: C += kappa_v T_v
-        // kappa_0 = alpha (1 - i), kappa_1 = alpha (-1 - i), kappa_2 = alpha i
-        const double kr = v == 0 ? g.ar + g.ai : (v == 1 ? g.ai - g.ar : -g.ai);
-        const double ki = v == 0 ? g.ai - g.ar : (v == 1 ? -g.ar - g.ai : g.ar);
-        if (row < P.M) {
-          const double sr = scales[e * scale_es + P.sa + (int64_t)v * P.tiles_m * OZ_BM + row];
-          const double* scn = scales + e * scale_es + P.sb + (int64_t)v * P.tiles_n * OZ_BN + col0;   // col0 includes the tile
-          // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
-          const int er = oz_expo(sr) - 1023 - 63;
-          c64* crow = C + (int64_t)row * P.ldc + col0;
-          const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
+      for (int c = 0; c < 3 * it.nchunk; ++c, ++cg) {
+        const int ab = cg % OZ_NBUF;
+        bool got = oz_wait(oz_su32(&sm.acc_full[ab]), (uint32_t)((cg / OZ_NBUF) & 1));
+        got = __all_sync(0xffffffffu, got);   // warp-uniform before the .sync.aligned TMEM loads
+        if (!got) {
+          if (lane == 0) atomicExch(flag, 3);
+          ok = false;
+          break;
+        }
+        if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-          for (int j = 0; j < OZ_DCOLS; ++j) {
-            if (col0 + j < P.N) {
-              // T sigma tau = (H 2^32 + L) 2^(-63 + log2 sigma + log2 tau), rounded once
-              const double tv = oz_fix_to_double(H[j], L[j], er + oz_expo(scn[j]) - 1023);
-              c64 o;
-              if (v == 0) {
-                o = make_double2(0.0, 0.0);
-                if (use_d) {
-                  const c64 dv = drow[j];
-                  o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
-                }
-              } else {
-                o = crow[j];
-              }
-              o.x = fma(kr, tv, o.x);
-              o.y = fma(ki, tv, o.y);
-              crow[j] = o;
-            }
-            if ((j & 3) == 3) asm volatile("" ::: "memory");   // keep the loads of later columns below
+        for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
+          // all 8 diagonals of 2 columns behind one wait
+          uint32_t r[OZ_ND][2];
+          const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ab * OZ_ACC + part * OZ_DCOLS + c0;
+#pragma unroll
+          for (int dg = 0; dg < OZ_ND; ++dg)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+                         : "=r"(r[dg][0]), "=r"(r[dg][1])
+                         : "r"(ta + dg * OZ_BN));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)); d >= 3 in
+            // b = sum v_d 2^(49 - 7 d) < 2^52.3, added to (H, L) with the carry out of the low word
+            long long x[OZ_ND];
+#pragma unroll
+            for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
+            const long long b = x[3] * (1ll << 28) + x[4] * (1ll << 21) + x[5] * (1ll << 14) + x[6] * (1ll << 7) + x[7];
+            const unsigned int lw = (unsigned int)b;
+            const unsigned int ln = L[c0 + j] + lw;
+            H[c0 + j] += x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32) + (ln < lw ? 1 : 0);
+            L[c0 + j] = ln;
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty[ab])) : "memory");
+        const int v = c / it.nchunk;
+        if (c % it.nchunk == it.nchunk - 1) {   // real product v complete: C += kappa_v T_v
+          // kappa_0 = alpha (1 - i), kappa_1 = alpha (-1 - i), kappa_2 = alpha i
+          const double kr = v == 0 ? g.ar + g.ai : (v == 1 ? g.ai - g.ar : -g.ai);
+          const double ki = v == 0 ? g.ai - g.ar : (v == 1 ? -g.ar - g.ai : g.ar);
+          if (row < P.M) {
+            const double sr = scales[e * scale_es + P.sa + (int64_t)v * P.tiles_m * OZ_BM + row];
+            const double* scn = scales + e * scale_es + P.sb + (int64_t)v * P.tiles_n * OZ_BN + col0;   // col0 includes the tile
+            // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
+            const int er = oz_expo(sr) - 1023 - 63;
+            c64* crow = C + (int64_t)row * P.ldc + col0;
+            const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
 #pragma unroll
-        for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
+            for (int j = 0; j < OZ_DCOLS; ++j) {
+              if (col0 + j < P.N) {
+                // T sigma tau = (H 2^32 + L) 2^(-63 + log2 sigma + log2 tau), rounded once
+                const double tv = oz_fix_to_double(H[j], L[j], er + oz_expo(scn[j]) - 1023);
+                c64 o;
+                if (v == 0) {
+                  o = make_double2(0.0, 0.0);
+                  if (use_d) {
+                    const c64 dv = drow[j];
+                    o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
+                  }
+                } else {
+                  o = crow[j];
+                }
+                o.x = fma(kr, tv, o.x);
+                o.y = fma(ki, tv, o.y);
+                crow[j] = o;
+              }
+              if ((j & 3) == 3) asm volatile("" ::: "memory");   // keep the loads of later columns below
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
+        }
       }
     }
   }
@@ -557,7 +596,15 @@ cudaError_t gemm_oz(const GemmArgs& g, int n_energy, uint16_t* slices, int64_t s
   }
   const size_t sm = sizeof(OzSmem) + 128;
   cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gemm_oz<<<dim3(g.total_tiles, n_energy), OZ_THREADS, sm, s>>>(g, slices, slice_es, scales, scale_es, flag);
+  static int sms[64] = {0};   // SM count per device (one resident CTA per SM: all of TMEM, ~200 KB)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  const long long items = (long long)g.total_tiles * n_energy;
+  if (items > 0x7fffffffll) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(items, std::max(sms[dev], 1));
+  k_gemm_oz<<<grid, OZ_THREADS, sm, s>>>(g, slices, slice_es, scales, scale_es, flag, (int)items);
   return cudaGetLastError();
 }
 
