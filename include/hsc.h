@@ -185,10 +185,11 @@ typedef enum {
                               /* per product list by a cost model, 1 = FP64 pipe only, 2 = FP64 */
                               /* emulation on the BF16 tensor cores wherever K > 0. The         */
                               /* emulation writes each real operand in eight balanced base-128  */
-                              /* digits (power-of-two row / column scales) and accumulates the  */
-                              /* digit products exactly; its error per K value is below 2^-52.5 */
-                              /* times the row and column maxima' powers of two, at the level   */
-                              /* of FP64 rounding.                                              */
+                              /* digits (one power-of-two scale per row of A and column of B for*/
+                              /* the real, imaginary and summed parts), accumulates the digit   */
+                              /* products exactly and combines the complex result exactly before*/
+                              /* one rounding per part; its error per K value and real product  */
+                              /* is below 2^-54.5 times the two scales, FP64 rounding level.    */
   HSC_OPT_RESOLVE_DIGITS = 7, /* d > 0: hsc_solve solves every energy whose residual (see      */
                               /* hsc_residual; default d = 10: on the 32^3 cube at eta = 1e-6   */
                               /* the default tree leaves 3 of 64 energies above 1e-10, the      */

@@ -4,10 +4,11 @@
 // Algorithms 59, 2012).
 //
 // C = alpha op(A) op(B) + beta D. The complex product is taken as three real products (3M):
-//     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),
-//     C = beta D + alpha [(1 - i) T0 + (-1 - i) T1 + i T2].
+//     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),   AB = (T0 - T1) + i (T2 - T0 - T1).
 // Each real product X Y (X: M x K, Y: K x N) is evaluated exactly up to a bounded truncation:
-//   * row i of X gets the power of two sigma_i > 2 max_k |X_ik|, column j of Y likewise tau_j;
+//   * row i of the three real operands Ar, Ai, Ar + Ai gets one power of two sigma_i > 2 max |.|
+//     over the row (columns j of Br, Bi, Br + Bi likewise tau_j), so that the three products are
+//     integers in the same units;
 //   * X_ik / sigma_i, a number in (-1/2, 1/2), is truncated towards zero to 56 fraction bits and
 //     written in balanced base-128 digits: X_ik = sigma_i (sum_s t_s 2^(-7 s) + delta), |delta| <
 //     2^-56, with OZ_S = 8 digits t_s in [-64, 63] (the leading one in [-65, 65]), each exact in
@@ -15,29 +16,32 @@
 //     slow);
 //   * a digit product t_s u_r has |t_s u_r| <= 65^2 and carries the weight 2^(-7 (s + r)); the
 //     products of one diagonal d = s + r (d <= OZ_S + 1: 36 pairs) accumulate in one FP32 tensor-
-//     memory accumulator, exact for 384 K values (at most 8 pairs: 8 * 65^2 * 384 < 2^24; the
-//     balanced digits give four times the headroom of digits in [0, 127]); every 384 K values the
-//     8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe would otherwise
-//     bound the kernel), into the 96-bit integer T 2^63 = H 2^32 + L per element (int64 H,
-//     uint32 L; diagonal d carries the weight 2^(49 - 7 d)); once per product T sigma_i tau_j is
-//     rounded to the nearest double, also on the integer pipe (the scales are powers of two), the
-//     only rounding;
-//   * per K value the error is below 2^-54.5 sigma_i tau_j (2^-52.5 times the products of the row
-//     and column maxima' powers of two): 2^-56 from the truncations (|X_ik| < sigma_i / 2) and
-//     2^-55.2 from the dropped diagonals d >= 10 (7 * 64^2 * 2^-70 for d = 10, less beyond).
+//     memory accumulator, exact for 384 K values (at most 8 pairs: 8 * 65^2 * 384 < 2^24); every
+//     384 K values the 8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe
+//     would otherwise bound the kernel), and added to or subtracted from the two 96-bit integers
+//     X 2^63 = H 2^32 + L (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)) of the
+//     complex result's real and imaginary parts (Re = T0 - T1, Im = T2 - T0 - T1, exact);
+//   * once per output element each part times sigma_i tau_j is rounded to the nearest double, also
+//     on the integer pipe (the scales are powers of two), the only rounding of the product; alpha
+//     and beta D are applied in FP64 and C is written once;
+//   * per K value and real product the error is below 2^-54.5 sigma_i tau_j: 2^-56 from the
+//     truncations (|X_ik| < sigma_i / 2) and 2^-55.2 from the dropped diagonals d >= 10
+//     (7 * 64^2 * 2^-70 for d = 10, less beyond); the real part carries two such errors, the
+//     imaginary part three.
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
-// op(A) (all 8 slices, 32 KB) and a 64 x 16 block of op(B)^T (16 KB) in the K-major core-matrix
+// op(A) (all 8 slices, 32 KB) and a 32 x 16 block of op(B)^T (8 KB) in the K-major core-matrix
 // layout the MMA reads, for each of the three real operands (re, im, re + im), reading each complex
 // element once per pass and writing 16-byte runs.
-// Pass 2 (k_gemm_oz), one CTA per 128 x 64 output tile: warp 0 streams the slice blocks of the three
-// real products one after another through a 4-stage ring (cp.async.bulk, mbarrier transaction
-// counts), warp 1 issues the 36 digit products of each K step as 12 MMAs of N = 64..256 (for each
-// A digit, the B digit planes it pairs with are contiguous along N and their column blocks are
-// the diagonal accumulators it feeds) into the 8 diagonal accumulators (512 TMEM columns), warps
-// 2-17 drain them every 24 K steps (16 columns of exact state per thread)
-// and, after the last chunk of a real product, add its share to C (read-modify-write by the owning
-// thread, so C may alias D). Every mbarrier wait is bounded; on expiry the kernel raises the flag,
-// waits (bounded) for its own copies, frees tensor memory and returns.
+// Pass 2 (k_gemm_oz), persistent, one CTA per SM over the items (energy, 128 x 32 output tile):
+// warp 0 streams the slice blocks of the three real products one after another through a 5-stage
+// ring (cp.async.bulk, mbarrier transaction counts); warp 1 issues the 36 digit products of each K
+// step as 8 MMAs of N = 32..256 (for each A digit, the B digit planes it pairs with are contiguous
+// along N and their column blocks are the diagonal accumulators it feeds) into one of two sets of 8
+// diagonal accumulators (2 x 256 TMEM columns, so the drain of one chunk overlaps the MMAs of the
+// next); warps 2-17 drain them every 24 K steps (8 columns of exact complex state per thread) and
+// write each output once (read-modify-write by the owning thread, so C may alias D). Every mbarrier
+// wait is bounded; on expiry the kernel raises the flag, waits (bounded) for its own copies, frees
+// tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -52,10 +56,10 @@ constexpr int OZ_S = 8;                  // slices per operand
 constexpr int OZ_BITS = 7;               // bits per slice
 constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // fraction bits kept (56)
 constexpr int OZ_ND = OZ_S;              // accumulated diagonals d = 2 .. OZ_S + 1
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;
+constexpr int OZ_BM = 128, OZ_BN = 32, OZ_BK = 16;
 constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (all slices)
 constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
-constexpr int OZ_STAGES = 4;
+constexpr int OZ_STAGES = 5;
 constexpr int OZ_DRAIN = 24;             // K steps per drain (384 K values)
 constexpr int OZ_TMAX = 65;              // largest |digit|
 constexpr int OZ_ACC = OZ_ND * OZ_BN;     // TMEM columns of one set of accumulators
@@ -211,15 +215,16 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
       e1 = max(e1, oz_expo(x.y));
       e2 = max(e2, oz_expo(x.x + x.y));
     }
-    if (e0) atomicMax(&s_e[0][r], e0);
-    if (e1) atomicMax(&s_e[1][r], e1);
-    if (e2) atomicMax(&s_e[2][r], e2);
+    // one scale per row for all three real operands, so that their products are exact integers in
+    // the same units and the complex result can be combined before any rounding
+    const int em = max(e0, max(e1, e2));
+    if (em) atomicMax(&s_e[0][r], em);
   }
   __syncthreads();
   // sigma = 2^(E - 1021) > 2 |x| for every x of the row with biased exponent <= E
   for (int i = tid; i < 3 * rows; i += OZP_THREADS) {
     const int v = i / rows, r = i % rows;
-    sc[v * sstride + r] = s_e[v][r] > 0 ? ldexp(1.0, s_e[v][r] - 1021) : 0.0;
+    sc[v * sstride + r] = s_e[0][r] > 0 ? ldexp(1.0, s_e[0][r] - 1021) : 0.0;
   }
   // pass 2: slices, 8 consecutive k of one row per task
   for (int t = tid; t < ntask; t += OZP_THREADS) {
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
         const int ex = (int)((bits >> 52) & 0x7FF);
         // floor(|x| / sigma * 2^56) < 2^55: |x| = mant 2^(ex - 1075), sigma = 2^(E - 1021), so the
         // 53-bit significand moves right by E - ex + 52 - 56 + 2 (a left shift of at most 2)
-        const int shift = s_e[v][r] - ex + (52 - OZ_FRAC + 2);
+        const int shift = s_e[0][r] - ex + (52 - OZ_FRAC + 2);
         const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
         const long long mag = (ex > 0 && shift < 64) ? (long long)(shift >= 0 ? mant >> shift : mant << (-shift)) : 0ll;
         m[q] = (bits >> 63) ? -mag : mag;
@@ -415,22 +420,16 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = oz_su32(&sm.a[st][0]), b0 = oz_su32(&sm.b[st][0]);
-            // The B digit planes r = 1..8 lie one after another along N (64 rows each, the same core-
-            // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 64 (9 - s): its
-            // column block r lands in the accumulator of diagonal s + r, which starts at TMEM column
-            // 64 (s + r - 2). One MMA per A digit (two where N would exceed 256): 12 per K step
-            // instead of 36, the same products.
+            // The B digit planes r = 1..8 lie one after another along N (32 rows each, the same core-
+            // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 32 (9 - s) <= 256:
+            // its column block r lands in the accumulator of diagonal s + r, which starts at TMEM
+            // column 32 (s + r - 2). 8 MMAs per K step instead of 36, the same products.
 #pragma unroll
             for (int si = 0; si < OZ_S; ++si) {
-              // the first MMAs of a chunk (si = 0) cover every diagonal and start the accumulation
+              // the first MMA of a chunk (si = 0) covers every diagonal and starts the accumulation
               const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
-              const uint64_t ad = oz_desc(a0 + si * (OZ_BM * OZ_BK * 2));
-              const int nr = OZ_S - si;              // B digit planes paired with A digit si + 1
-              const int q0 = nr < 4 ? nr : 4;
-              oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, ad, oz_desc(b0), idesc_n(q0), acc);
-              if (nr > 4)
-                oz_mma(tmem + ab * OZ_ACC + (si + 4) * OZ_BN, ad, oz_desc(b0 + 4 * (OZ_BN * OZ_BK * 2)),
-                       idesc_n(nr - 4), acc);
+              oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)), oz_desc(b0),
+                     idesc_n(OZ_S - si), acc);
             }
             oz_commit(oz_su32(&sm.empty[st]));
           }
@@ -451,12 +450,16 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
       const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
       const int col0 = it.tn * OZ_BN + part * OZ_DCOLS;
-      // exact running sum T 2^63 = H 2^32 + L of the chunks; |H| < nchunk 2^41.6, exact in FP64 for
-      // nchunk < 2^11 (K < 786432)
-      long long H[OZ_DCOLS];
-      unsigned int L[OZ_DCOLS];
+      // exact running sums of the complex result, Re = T0 - T1 and Im = T2 - T0 - T1 (3M): the three
+      // real operands of a row (and of a column) share one power-of-two scale, so the digit products
+      // of the three real products are integers in the same units. Each sum is the 96-bit integer
+      // X 2^63 = H 2^32 + L (int64 H, uint32 L); |H| < 3 nchunk 2^42, exact in FP64 for
+      // nchunk < 2^9 (K < 196608).
+      long long Hr[OZ_DCOLS], Hi[OZ_DCOLS];
+      unsigned int Lr[OZ_DCOLS], Li[OZ_DCOLS];
 #pragma unroll
-      for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
+      for (int j = 0; j < OZ_DCOLS; ++j) { Hr[j] = 0; Hi[j] = 0; Lr[j] = 0u; Li[j] = 0u; }
+      const int last = 3 * it.nchunk - 1;
       if (it.ks == 0 && row < P.M) {   // C = beta D
         for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
           c64 o = make_double2(0.0, 0.0);
@@ -481,6 +484,9 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        // real product v of the chunk: T0 adds to Re and subtracts from Im, T1 subtracts from both,
+        // T2 adds to Im
+        const int v = c / it.nchunk;
 #pragma unroll
         for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
           // all 8 diagonals of 2 columns behind one wait
@@ -494,57 +500,70 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            // weight of diagonal d in T 2^63: 2^(49 - 7 d); d <= 2 lands in H (2^(17 - 7 d)); d >= 3 in
-            // b = sum v_d 2^(49 - 7 d) < 2^52.3, added to (H, L) with the carry out of the low word
+            // weight of diagonal d in X 2^63: 2^(49 - 7 d); the chunk's value is Hc 2^32 + Lc with
+            // b = sum_{d >= 3} v_d 2^(49 - 7 d) (|b| < 2^52.3) split at bit 32
             long long x[OZ_ND];
 #pragma unroll
             for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
             const long long b = x[3] * (1ll << 28) + x[4] * (1ll << 21) + x[5] * (1ll << 14) + x[6] * (1ll << 7) + x[7];
-            const unsigned int lw = (unsigned int)b;
-            const unsigned int ln = L[c0 + j] + lw;
-            H[c0 + j] += x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32) + (ln < lw ? 1 : 0);
-            L[c0 + j] = ln;
+            const unsigned int lc = (unsigned int)b;
+            const long long hc = x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32);
+            const int q = c0 + j;
+            if (v == 0) {        // Re += T0
+              const unsigned int ln = Lr[q] + lc;
+              Hr[q] += hc + (ln < lc ? 1 : 0);
+              Lr[q] = ln;
+            } else if (v == 1) { // Re -= T1
+              const unsigned int ln = Lr[q] - lc;
+              Hr[q] -= hc + (Lr[q] < lc ? 1 : 0);
+              Lr[q] = ln;
+            }
+            if (v == 2) {        // Im += T2
+              const unsigned int ln = Li[q] + lc;
+              Hi[q] += hc + (ln < lc ? 1 : 0);
+              Li[q] = ln;
+            } else {             // Im -= T0, Im -= T1
+              const unsigned int ln = Li[q] - lc;
+              Hi[q] -= hc + (Li[q] < lc ? 1 : 0);
+              Li[q] = ln;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty[ab])) : "memory");
-        const int v = c / it.nchunk;
-        if (c % it.nchunk == it.nchunk - 1) {   // real product v complete: C += kappa_v T_v
-          // kappa_0 = alpha (1 - i), kappa_1 = alpha (-1 - i), kappa_2 = alpha i
-          const double kr = v == 0 ? g.ar + g.ai : (v == 1 ? g.ai - g.ar : -g.ai);
-          const double ki = v == 0 ? g.ai - g.ar : (v == 1 ? -g.ar - g.ai : g.ar);
-          if (row < P.M) {
-            const double sr = scales[e * scale_es + P.sa + (int64_t)v * P.tiles_m * OZ_BM + row];
-            const double* scn = scales + e * scale_es + P.sb + (int64_t)v * P.tiles_n * OZ_BN + col0;   // col0 includes the tile
-            // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
-            const int er = oz_expo(sr) - 1023 - 63;
-            c64* crow = C + (int64_t)row * P.ldc + col0;
-            const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
+        if (c == last && row < P.M) {   // the complex result, rounded once per part: C = alpha X + beta D
+          const double sr = scales[e * scale_es + P.sa + row];
+          const double* scn = scales + e * scale_es + P.sb + col0;   // col0 includes the tile
+          // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
+          const int er = oz_expo(sr) - 1023 - 63;
+          c64* crow = C + (int64_t)row * P.ldc + col0;
+          const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
+          const bool real_ab = g.ai == 0.0 && g.bi == 0.0;
 #pragma unroll
-            for (int j = 0; j < OZ_DCOLS; ++j) {
-              if (col0 + j < P.N) {
-                // T sigma tau = (H 2^32 + L) 2^(-63 + log2 sigma + log2 tau), rounded once
-                const double tv = oz_fix_to_double(H[j], L[j], er + oz_expo(scn[j]) - 1023);
-                c64 o;
-                if (v == 0) {
-                  o = make_double2(0.0, 0.0);
-                  if (use_d) {
-                    const c64 dv = drow[j];
-                    o = make_double2(g.br * dv.x - g.bi * dv.y, g.br * dv.y + g.bi * dv.x);
-                  }
-                } else {
-                  o = crow[j];
+          for (int j = 0; j < OZ_DCOLS; ++j) {
+            if (col0 + j < P.N) {
+              const int es = er + oz_expo(scn[j]) - 1023;
+              const double xr = oz_fix_to_double(Hr[j], Lr[j], es), xi = oz_fix_to_double(Hi[j], Li[j], es);
+              c64 o;
+              if (real_ab) {
+                o = make_double2(g.ar * xr, g.ar * xi);
+                if (use_d) {
+                  const c64 dv = drow[j];
+                  o.x = fma(g.br, dv.x, o.x);
+                  o.y = fma(g.br, dv.y, o.y);
                 }
-                o.x = fma(kr, tv, o.x);
-                o.y = fma(ki, tv, o.y);
-                crow[j] = o;
+              } else {
+                o = make_double2(g.ar * xr - g.ai * xi, g.ar * xi + g.ai * xr);
+                if (use_d) {
+                  const c64 dv = drow[j];
+                  o.x += g.br * dv.x - g.bi * dv.y;
+                  o.y += g.br * dv.y + g.bi * dv.x;
+                }
               }
-              if ((j & 3) == 3) asm volatile("" ::: "memory");   // keep the loads of later columns below
+              crow[j] = o;
             }
           }
-#pragma unroll
-          for (int j = 0; j < OZ_DCOLS; ++j) { H[j] = 0; L[j] = 0u; }
         }
       }
     }

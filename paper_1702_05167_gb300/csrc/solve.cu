@@ -204,12 +204,12 @@ constexpr int TILE = 64;
 
 // Per-SM cost model of the two FP64-accurate engines in FP64-pipe operations (DFMA equivalents,
 // 1.9 DFMA per clock and SM): the FP64 pipe does 3 (4) K DFMA per element of a 64x64 tile; the
-// emulation does, per 128x64 tile and real product, 12 MMAs of 128x(64..256)x16 per 16 K values
-// (the 36 digit products, ~30 clocks each on average), then one integer drain per 384 K values
-// (~0.8 clocks per element; the MMAs wait for it), an epilogue of ~3 FP64-pipe operations per
-// element, plus the slicing pass (about 9 DFMA-times per operand element at HBM speed).
-constexpr double OZ_TILE = 128 * 64, OZ_DRAIN_DFMA = OZ_TILE * 0.8 * 1.9, OZ_MMA_DFMA = 30 * 1.9,
-                 OZ_EPI_DFMA = OZ_TILE * 3.0, OZ_PACK_DFMA = 9.0;
+// emulation does, per 128x32 tile and real product, 8 MMAs of 128x(32..256)x16 per 16 K values (the
+// 36 digit products, ~600 clocks per K step), one integer drain per 384 K values overlapped with
+// the MMAs, one epilogue of ~6 FP64-pipe operations per element, plus the slicing pass (about 9
+// DFMA-times per operand element at HBM speed).
+constexpr double OZ_TILE = 128 * 32, OZ_DRAIN_DFMA = OZ_TILE * 0.3 * 1.9, OZ_MMA_DFMA = 17 * 1.9,
+                 OZ_EPI_DFMA = OZ_TILE * 6.0, OZ_PACK_DFMA = 9.0;
 
 struct GemmList {
   std::vector<GemmProb>& all;      // 64x64-tile problem lists
@@ -255,8 +255,8 @@ struct GemmList {
     const double tz = (double)((M + TILE - 1) / TILE) * p.tiles_n * TILE * TILE;
     cost_z += tz * 3.0 * K;
     const double nt = tilesoz - t0;
-    cost_oz += nt * 3.0 * (std::ceil(K / 384.0) * OZ_DRAIN_DFMA + std::ceil(K / 16.0) * 36 * OZ_MMA_DFMA +
-                           OZ_EPI_DFMA) +
+    cost_oz += nt * (3.0 * (std::ceil(K / 384.0) * OZ_DRAIN_DFMA + std::ceil(K / 16.0) * 36 * OZ_MMA_DFMA) +
+                     OZ_EPI_DFMA) +
                ((double)M * K + (double)K * N) * OZ_PACK_DFMA;
     all.push_back(p);
     all128.push_back(q);

@@ -90,8 +90,9 @@ def test_tcgen05_3xtf32_engine(lib, oa, ob, M, N, K):
 @pytest.mark.parametrize("oa,ob", OPS)
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_fp64_emulation_engine(lib, oa, ob, M, N, K):
-    """Eight balanced base-128 digits on the BF16 tensor cores: per K value the error is below
-    2^-52.5 times the row and column maxima's powers of two, so at FP64 level of |A||B|."""
+    """Eight balanced base-128 digits on the BF16 tensor cores: per K value and real product the
+    error is below 2^-54.5 times the row and column scales (at most 8x the complex maxima's powers
+    of two), so at FP64 level of |A||B|."""
     err = run(lib, 4, oa, ob, M, N, K, M + N + K)
     assert err <= 1e-13, err
 
@@ -145,12 +146,21 @@ def test_fp64_emulation_full_digits(lib, K):
     assert np.max(np.abs(C.real - float(K * kept))) <= K * 2.0 ** -50
 
 
+def _scheme_scales(X, axis):
+    """The emulation's power-of-two scale of each row (axis 1) or column (axis 0): one for the three
+    real operands re, im and re + im, 4 times the power of two at or below their largest |entry|."""
+    m = np.maximum(np.maximum(np.abs(X.real), np.abs(X.imag)), np.abs(X.real + X.imag)).max(axis=axis)
+    return np.where(m > 0, 2.0 ** (np.floor(np.log2(np.where(m > 0, m, 1))) + 2), 0.0)
+
+
 def test_fp64_emulation_within_row_dynamic_range(lib):
     """Entries of one row of A (and of one column of B) spanning 2^-40 .. 1: the emulation keeps 56
-    bits relative to each row's and column's largest power of two, so its error obeys
-    |C - AB| <= K 2^-52.5 rowmax(|A|) colmax(|B|) (the documented bound; a componentwise
-    K u |A||B| bound does not hold for entries far below their row's maximum, which keep fewer
-    bits)."""
+    bits relative to each row's and column's scale (sigma_i, tau_j: powers of two above twice the
+    row's or column's largest real or imaginary part), so per K value and real product its error is
+    below 2^-54.5 sigma_i tau_j, and the imaginary part of the complex product carries three real
+    products: |C - AB| <= 3 K 2^-54.5 sigma_i tau_j plus the final rounding (the documented bound;
+    a componentwise K u |A||B| bound does not hold for entries far below their row's maximum,
+    which keep fewer bits)."""
     rng = np.random.default_rng(11)
     M, N, K = 96, 80, 700
     mag = lambda *sh: 2.0 ** rng.uniform(-40, 0, sh)
@@ -158,9 +168,9 @@ def test_fp64_emulation_within_row_dynamic_range(lib):
     B = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * mag(K, N)
     C = _emulated(lib, A, B)
     ref = A @ B
-    pw = lambda a, ax: 2.0 ** np.ceil(np.log2(np.max(np.abs(a), axis=ax)))
-    bound = 16 * K * pw(A, 1)[:, None] * pw(B, 0)[None, :] * 2.0 ** -52.5   # 3 real products, scales <= 4 pw
-    assert np.all(np.abs(C - ref) <= bound)
+    bound = 3 * K * 2.0 ** -54.5 * _scheme_scales(A, 1)[:, None] * _scheme_scales(B, 0)[None, :] + \
+        2.0 ** -52 * np.abs(ref)
+    assert np.all(np.abs(C.real - ref.real) <= bound) and np.all(np.abs(C.imag - ref.imag) <= bound)
 
 
 def test_fp64_emulation_row_scaling(lib):
