@@ -142,16 +142,22 @@ class Surrogate:
 
 
 def adaptive_grid(sur, feats, n_points, fine=8192, floor=1.0, window=WINDOW):
-    """Energies at equal quantiles of rho = |T''|^(1/3)/mean + |D''|^(1/3)/mean + floor, with T
-    and D the surrogate's transmission and DOS on a fine uniform grid (endpoints included)."""
+    """Energies at equal quantiles of rho = |T''|^(1/3)/s_T + |D''|^(1/3)/s_D + floor, with T and D
+    the surrogate's transmission and DOS on a fine uniform grid (endpoints included). Each curvature
+    term is normalised by s = max(its mean, (range / window^2)^(1/3)): the curvature a function of
+    that range would have if it bent once over the window. A function with no curvature (constant
+    or linear), whose discrete second derivative is rounding noise, then adds ~nothing instead of
+    having its noise scaled to O(1) by its own tiny mean."""
     Ef = np.linspace(window[0], window[1], fine)
     pred = sur.predict(np.column_stack([Ef, np.tile(feats, (fine, 1))]))
     T = 10.0 ** pred[:, 0]
     Dn = pred[:, 1]
     h = Ef[1] - Ef[0]
+    L = window[1] - window[0]
     d2 = lambda y: np.abs(np.gradient(np.gradient(y, h), h)) ** (1 / 3)
+    scale = lambda c, y: max(c.mean(), (np.ptp(y) / (L * L)) ** (1 / 3), 1e-300)
     a, b = d2(T), d2(Dn)
-    rho = a / max(a.mean(), 1e-300) + b / max(b.mean(), 1e-300) + floor
+    rho = a / scale(a, T) + b / scale(b, Dn) + floor
     cdf = np.concatenate([[0.0], np.cumsum(0.5 * (rho[1:] + rho[:-1]) * h)])
     cdf /= cdf[-1]
     return np.interp(np.linspace(0, 1, n_points), cdf, Ef)
