@@ -13,6 +13,10 @@ __host__ __device__ inline c64 cadd(c64 a, c64 b) { return make_double2(a.x + b.
 __host__ __device__ inline c64 csub(c64 a, c64 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __host__ __device__ inline c64 cconj(c64 a) { return make_double2(a.x, -a.y); }
 __host__ __device__ inline c64 cneg(c64 a) { return make_double2(-a.x, -a.y); }
+// a - f p in four fused multiply-adds (two roundings per part instead of three)
+__host__ __device__ inline c64 cfms(c64 a, c64 f, c64 p) {
+  return make_double2(fma(-f.x, p.x, fma(f.y, p.y, a.x)), fma(-f.x, p.y, fma(-f.y, p.x, a.y)));
+}
 
 // One problem of a grouped GEMM:  C = alpha * op(A) op(B) + beta * D   (D rows in [zr0, zr1) are
 // treated as zero). Offsets are element offsets inside the per-energy slice of each operand array.

@@ -21,9 +21,13 @@
 //     would otherwise bound the kernel), and added to or subtracted from the two 96-bit integers
 //     X 2^63 = H 2^32 + L (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)) of the
 //     complex result's real and imaginary parts (Re = T0 - T1, Im = T2 - T0 - T1, exact);
-//   * once per output element each part times sigma_i tau_j is rounded to the nearest double, also
-//     on the integer pipe (the scales are powers of two), the only rounding of the product; alpha
-//     and beta D are applied in FP64 and C is written once;
+//   * for alpha = +-2^a and beta = 0 or +-2^b (real: every product of the solver) the chunks are
+//     added with alpha's sign, beta D / 2^a rounded to the sums' units (2^-63 sigma_i tau_j) is
+//     added after the last one, and once per output element each part is rounded to the nearest
+//     double on the integer pipe (the scales are powers of two): C = alpha X + beta D with one
+//     rounding. Other
+//     alpha, beta (and D beyond 2^31 sigma_i tau_j, a zero scale, a non-finite D) round X and apply
+//     alpha and beta D in FP64; C is written once;
 //   * per K value and real product the error is below 2^-54.5 sigma_i tau_j: 2^-56 from the
 //     truncations (|X_ik| < sigma_i / 2) and 2^-55.2 from the dropped diagonals d >= 10
 //     (7 * 64^2 * 2^-70 for d = 10, less beyond); the real part carries two such errors, the
@@ -130,6 +134,52 @@ __device__ __forceinline__ double oz_fix_to_double(long long H, unsigned int L, 
     return ldexp(fma((double)L, 0x1p-32, (double)H), es + 32);
   return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
                                           ((unsigned long long)biased << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// x = +-2^k exactly (x normal): k and the sign
+__device__ __forceinline__ bool oz_pow2(double x, int& k, bool& neg) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF || (bits & 0xFFFFFFFFFFFFFull) != 0ull) return false;
+  k = ex - 1023;
+  neg = (bits >> 63) != 0ull;
+  return true;
+}
+
+// (-1)^neg d / 2^es rounded to the nearest integer (ties away from zero), as the 96-bit H 2^32 + L;
+// false for a d that is not finite or whose value does not fit in 94 bits
+__device__ __forceinline__ bool oz_double_to_fix(double d, int es, bool neg, long long& H, unsigned int& L) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0x7FF) return false;
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (ex) m |= 1ull << 52;
+  if (m == 0ull) { H = 0; L = 0u; return true; }
+  const int sh = (ex ? ex : 1) - 1075 - es;   // d = m 2^(sh + es)
+  if (sh > 41) return false;
+  long long h;
+  unsigned int l;
+  if (sh >= 32) {
+    h = (long long)(m << (sh - 32));
+    l = 0u;
+  } else if (sh >= 0) {
+    h = (long long)(m >> (32 - sh));
+    l = (unsigned int)(m << sh);
+  } else if (sh > -54) {
+    const unsigned long long v = (m + (1ull << (-sh - 1))) >> (-sh);
+    h = (long long)(v >> 32);
+    l = (unsigned int)v;
+  } else {
+    h = 0;
+    l = 0u;
+  }
+  if (neg != ((bits >> 63) != 0ull)) {   // two's complement of the 96-bit value
+    l = ~l + 1u;
+    h = ~h + (l == 0u ? 1 : 0);
+  }
+  H = h;
+  L = l;
+  return true;
 }
 
 // element (r, k) of a rows x 16 K-major BF16 block: core matrices of 8 rows x 16 B (8 values); the
@@ -439,6 +489,15 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
     }
   } else {   // warps 2..: drain, TMEM lane quadrant = warp % 4, column part = (warp - 2) / 4
     const int quad = warp & 3, part = (warp - 2) >> 2;
+    // Integer epilogue when alpha = +-2^ka and beta = 0 or +-2^kb (real; every product of the solver):
+    // the sums hold alpha X / 2^ka (chunks added with alpha's sign), beta D / 2^ka is added to them
+    // in their units (rounded to 2^-63 sigma_i tau_j) after the last chunk, and the output is one
+    // rounding of the whole expression, on the integer pipe.
+    int ka = 0, kb = 0;
+    bool aneg = false, bneg = false;
+    const bool iep = g.ai == 0.0 && g.bi == 0.0 && oz_pow2(g.ar, ka, aneg) &&
+                     (g.br == 0.0 || oz_pow2(g.br, kb, bneg));
+    const bool xneg = iep && aneg;
     int cg = 0;   // chunks drained (all items)
     bool ok = true;
     for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
@@ -450,17 +509,9 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       const c64* D = g.D ? reinterpret_cast<const c64*>(g.D) + e * g.d_es + P.d : nullptr;
       const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
       const int col0 = it.tn * OZ_BN + part * OZ_DCOLS;
-      // exact running sums of the complex result, Re = T0 - T1 and Im = T2 - T0 - T1 (3M): the three
-      // real operands of a row (and of a column) share one power-of-two scale, so the digit products
-      // of the three real products are integers in the same units. Each sum is the 96-bit integer
-      // X 2^63 = H 2^32 + L (int64 H, uint32 L); |H| < 3 nchunk 2^42, exact in FP64 for
-      // nchunk < 2^9 (K < 196608).
-      long long Hr[OZ_DCOLS], Hi[OZ_DCOLS];
-      unsigned int Lr[OZ_DCOLS], Li[OZ_DCOLS];
-#pragma unroll
-      for (int j = 0; j < OZ_DCOLS; ++j) { Hr[j] = 0; Hi[j] = 0; Lr[j] = 0u; Li[j] = 0u; }
+      const bool in_row = row < P.M;
       const int last = 3 * it.nchunk - 1;
-      if (it.ks == 0 && row < P.M) {   // C = beta D
+      if (it.ks == 0 && in_row) {   // C = beta D
         for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
           c64 o = make_double2(0.0, 0.0);
           if (use_d) {
@@ -470,6 +521,15 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           C[(int64_t)row * P.ldc + col0 + j] = o;
         }
       }
+      // exact running sums of the complex result, Re = T0 - T1 and Im = T2 - T0 - T1 (3M): the three
+      // real operands of a row (and of a column) share one power-of-two scale, so the digit products
+      // of the three real products are integers in the same units. Each sum is the 96-bit integer
+      // H 2^32 + L (int64 H, uint32 L); the products contribute |H| < 3 nchunk 2^42 and beta D at
+      // most 2^62 (larger D takes the FP64 path).
+      long long Hr[OZ_DCOLS], Hi[OZ_DCOLS];
+      unsigned int Lr[OZ_DCOLS], Li[OZ_DCOLS];
+#pragma unroll
+      for (int j = 0; j < OZ_DCOLS; ++j) { Hr[j] = 0; Hi[j] = 0; Lr[j] = 0u; Li[j] = 0u; }
       for (int c = 0; c < 3 * it.nchunk; ++c, ++cg) {
         const int ab = cg % OZ_NBUF;
         bool got = oz_wait(oz_su32(&sm.acc_full[ab]), (uint32_t)((cg / OZ_NBUF) & 1));
@@ -485,7 +545,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         // real product v of the chunk: T0 adds to Re and subtracts from Im, T1 subtracts from both,
-        // T2 adds to Im
+        // T2 adds to Im (each chunk value negated first for a negative alpha on the integer path)
         const int v = c / it.nchunk;
 #pragma unroll
         for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
@@ -502,12 +562,18 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           for (int j = 0; j < 2; ++j) {
             // weight of diagonal d in X 2^63: 2^(49 - 7 d); the chunk's value is Hc 2^32 + Lc with
             // b = sum_{d >= 3} v_d 2^(49 - 7 d) (|b| < 2^52.3) split at bit 32
-            long long x[OZ_ND];
+            int x[OZ_ND];
 #pragma unroll
             for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
-            const long long b = x[3] * (1ll << 28) + x[4] * (1ll << 21) + x[5] * (1ll << 14) + x[6] * (1ll << 7) + x[7];
-            const unsigned int lc = (unsigned int)b;
-            const long long hc = x[0] * (1ll << 17) + x[1] * (1ll << 10) + x[2] * (1ll << 3) + (b >> 32);
+            const long long b = (long long)x[3] * (1ll << 28) + (long long)x[4] * (1ll << 21) +
+                                (long long)x[5] * (1ll << 14) + (long long)(x[6] * 128 + x[7]);
+            unsigned int lc = (unsigned int)b;
+            long long hc = (long long)x[0] * (1ll << 17) + (long long)x[1] * (1ll << 10) +
+                           (long long)x[2] * (1ll << 3) + (b >> 32);
+            if (xneg) {   // alpha < 0: the chunk's value negated (96-bit two's complement)
+              hc = -hc - (lc != 0u ? 1 : 0);
+              lc = 0u - lc;
+            }
             const int q = c0 + j;
             if (v == 0) {        // Re += T0
               const unsigned int ln = Lr[q] + lc;
@@ -532,33 +598,49 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&sm.acc_empty[ab])) : "memory");
-        if (c == last && row < P.M) {   // the complex result, rounded once per part: C = alpha X + beta D
-          const double sr = scales[e * scale_es + P.sa + row];
-          const double* scn = scales + e * scale_es + P.sb + col0;   // col0 includes the tile
-          // the scales are powers of two (or 0 for an all-zero row / column, whose sums are 0)
-          const int er = oz_expo(sr) - 1023 - 63;
+        if (c == last && in_row) {   // the result, rounded once per part
           c64* crow = C + (int64_t)row * P.ldc + col0;
           const c64* drow = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
-          const bool real_ab = g.ai == 0.0 && g.bi == 0.0;
+          // units of the sums of column j: 2^es, es = (row exponent - 1023 - 63) + (column exponent -
+          // 1023) (+ ka); a zero scale (an all-zero row or column) makes the product 0 and the element
+          // takes the FP64 path, as do a D beyond 2^31 sigma_i tau_j and a non-finite D
+          const int er2 = oz_expo(scales[e * scale_es + P.sa + row]);
+          const double* scn = scales + e * scale_es + P.sb + col0;
 #pragma unroll
           for (int j = 0; j < OZ_DCOLS; ++j) {
             if (col0 + j < P.N) {
-              const int es = er + oz_expo(scn[j]) - 1023;
-              const double xr = oz_fix_to_double(Hr[j], Lr[j], es), xi = oz_fix_to_double(Hi[j], Li[j], es);
-              c64 o;
-              if (real_ab) {
-                o = make_double2(g.ar * xr, g.ar * xi);
-                if (use_d) {
-                  const c64 dv = drow[j];
-                  o.x = fma(g.br, dv.x, o.x);
-                  o.y = fma(g.br, dv.y, o.y);
+              const int ecj = oz_expo(scn[j]);
+              const int es = er2 - 1023 - 63 + ecj - 1023 + (iep ? ka : 0);
+              bool f = !iep || er2 == 0 || ecj == 0;
+              if (!f && use_d) {   // fold beta D / 2^ka into the sums
+                const c64 d = drow[j];
+                long long h0, h1;
+                unsigned int l0, l1;
+                f = !oz_double_to_fix(d.x, es - kb, bneg, h0, l0) || !oz_double_to_fix(d.y, es - kb, bneg, h1, l1);
+                if (!f) {
+                  unsigned int ln = Lr[j] + l0;
+                  Hr[j] += h0 + (ln < l0 ? 1 : 0);
+                  Lr[j] = ln;
+                  ln = Li[j] + l1;
+                  Hi[j] += h1 + (ln < l1 ? 1 : 0);
+                  Li[j] = ln;
                 }
-              } else {
-                o = make_double2(g.ar * xr - g.ai * xi, g.ar * xi + g.ai * xr);
+              }
+              const double xr = oz_fix_to_double(Hr[j], Lr[j], es), xi = oz_fix_to_double(Hi[j], Li[j], es);
+              c64 o = make_double2(xr, xi);
+              if (f) {
+                const bool real_ab = g.ai == 0.0 && g.bi == 0.0;
+                if (!iep) o = real_ab ? make_double2(g.ar * xr, g.ar * xi)
+                                      : make_double2(g.ar * xr - g.ai * xi, g.ar * xi + g.ai * xr);
                 if (use_d) {
-                  const c64 dv = drow[j];
-                  o.x += g.br * dv.x - g.bi * dv.y;
-                  o.y += g.br * dv.y + g.bi * dv.x;
+                  const c64 d = drow[j];
+                  if (real_ab) {
+                    o.x = fma(g.br, d.x, o.x);
+                    o.y = fma(g.br, d.y, o.y);
+                  } else {
+                    o.x += g.br * d.x - g.bi * d.y;
+                    o.y += g.br * d.y + g.bi * d.x;
+                  }
                 }
               }
               crow[j] = o;

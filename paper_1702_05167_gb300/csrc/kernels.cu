@@ -136,6 +136,7 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   __shared__ int s_i[GJ_THREADS / 32];
   __shared__ int s_p;
   __shared__ c64 s_inv;
+  __shared__ c64 s_pr[64];   // the scaled new row j (panel width <= 64)
   for (int j = k0; j < k0 + w; ++j) {
     double best = -1.0;
     int bi = n;
@@ -173,17 +174,18 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
     for (int c = tid; c < w; c += GJ_THREADS) {
       const c64 a = A[(int64_t)p * ld + k0 + c];
       if (p != j) A[(int64_t)p * ld + k0 + c] = A[(int64_t)j * ld + k0 + c];
-      A[(int64_t)j * ld + k0 + c] = (k0 + c == j) ? inv : cmul(a, inv);
+      const c64 nv = (k0 + c == j) ? inv : cmul(a, inv);
+      A[(int64_t)j * ld + k0 + c] = nv;
+      s_pr[c] = nv;
     }
     __syncthreads();
     for (int r = tid; r < n; r += GJ_THREADS) {
       if (r == j) continue;
       c64* row = A + (int64_t)r * ld;
       const c64 f = row[j];
-      const c64* pr = A + (int64_t)j * ld;
       for (int c = 0; c < w; ++c) {
         if (k0 + c == j) continue;
-        row[k0 + c] = csub(row[k0 + c], cmul(f, pr[k0 + c]));
+        row[k0 + c] = cfms(row[k0 + c], f, s_pr[c]);
       }
       row[j] = cneg(cmul(f, inv));
     }
@@ -298,7 +300,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
       const c64 f = row[j];
       for (int c = 0; c < w; ++c) {
         if (k0 + c == j) continue;
-        row[k0 + c] = csub(row[k0 + c], cmul(f, s_pr[c]));
+        row[k0 + c] = cfms(row[k0 + c], f, s_pr[c]);
       }
       row[j] = cneg(cmul(f, inv));
     }

@@ -184,3 +184,80 @@ def test_fp64_emulation_row_scaling(lib):
     ref = A @ B
     bound = K * np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :] * 2.0 ** -46
     assert np.all(np.abs(C - ref) <= bound)
+
+
+def _emulated_ab(L, A, B, Dm, alpha, beta, inplace=False):
+    """C = alpha A B + beta D on the emulation engine (op N, N); D may be C itself (in place)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    dv = torch.device("cuda")
+    tA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.complex128).view(np.float64)).to(dv)
+    tB = torch.from_numpy(np.ascontiguousarray(B, dtype=np.complex128).view(np.float64)).to(dv)
+    tD = torch.from_numpy(np.ascontiguousarray(Dm, dtype=np.complex128).view(np.float64)).to(dv)
+    tC = tD if inplace else torch.full((M, 2 * N), float("nan"), dtype=torch.float64, device=dv)
+    code = L.hsc_debug_gemm(4, 0, 0, M, N, K, tA.data_ptr(), K, tB.data_ptr(), N, tC.data_ptr(), N,
+                            tD.data_ptr(), N, alpha.real, alpha.imag, beta.real, beta.imag, None)
+    assert code == 0, hsc.hsc_last_error()
+    return tC.cpu().numpy().view(np.complex128)
+
+
+@pytest.mark.parametrize("alpha,beta", [(1, 1), (-1, 1), (1, -1), (-1, -1), (0.5, -1), (-2, 0.25),
+                                        (1, 0), (-0.5, 0), (0.7, 1), (1, 0.3 + 0.1j)])
+@pytest.mark.parametrize("M,N,K", [(5, 7, 3), (130, 257, 33), (300, 200, 517)])
+def test_fp64_emulation_alpha_beta(lib, alpha, beta, M, N, K):
+    """alpha = +-2^k with beta = 0 or +-2^k (every product of the solve) takes the integer epilogue:
+    beta D is folded into the exact sums in the product's units and the result rounded once; other
+    alpha, beta take the FP64 epilogue. Both at 1e-13 of |alpha||A||B| + |beta D| componentwise,
+    also with C aliasing D."""
+    rng = np.random.default_rng(M * N + K)
+    cplx = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    A, B, Dm = cplx(M, K), cplx(K, N), cplx(M, N)
+    alpha, beta = complex(alpha), complex(beta)
+    ref = alpha * (A @ B) + beta * Dm
+    scale = np.abs(alpha) * np.abs(A) @ np.abs(B) + np.abs(beta * Dm)
+    for inplace in (False, True):
+        C = _emulated_ab(lib, A, B, Dm, alpha, beta, inplace)
+        assert np.max(np.abs(C - ref) / scale) <= 1e-13
+
+
+def test_fp64_emulation_integer_epilogue_is_one_rounding(lib):
+    """Small integers: alpha A B + beta D is an exact double, and the integer epilogue (one rounding
+    of the whole expression) must return it bit for bit, for every sign combination and a power-of-
+    two alpha; D entries of 2^40 sit far above the product's units and still fold in exactly."""
+    rng = np.random.default_rng(5)
+    M, N, K = 140, 70, 300
+    ints = lambda *s: rng.integers(-15, 16, s) + 1j * rng.integers(-15, 16, s)
+    A, B = ints(M, K), ints(K, N)
+    Dm = ints(M, N) * 2.0 ** rng.integers(0, 41, (M, N))
+    for alpha, beta in ((1, 1), (-1, 1), (1, -1), (-1, -1), (0.5, -1), (-4, 0.5)):
+        alpha, beta = complex(alpha), complex(beta)
+        C = _emulated_ab(lib, A, B, Dm, alpha, beta)
+        assert np.array_equal(C, alpha * (A @ B) + beta * Dm)
+
+
+def test_fp64_emulation_epilogue_fallbacks(lib):
+    """Elements the integer epilogue cannot fold take the FP64 one: D far above the product's
+    range (|D| = 2^200 times the row and column scales), an all-zero row of A or column of B (zero
+    scale: C = beta D exactly), and non-finite D (inf propagates); tiny and subnormal D fold in with
+    a rounding at 2^-63 of the scales."""
+    rng = np.random.default_rng(9)
+    M, N, K = 130, 66, 200
+    cplx = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    A, B, Dm = cplx(M, K), cplx(K, N), cplx(M, N)
+    A[7, :] = 0
+    B[:, 40] = 0
+    Dm[3, :8] *= 2.0 ** 200
+    Dm[5, 10:20] = 5e-310 - 3e-320j
+    Dm[9, 30:34] *= 2.0 ** -600
+    Dm[11, 50] = np.inf
+    alpha, beta = complex(-1), complex(1)
+    with np.errstate(invalid="ignore"):
+        ref = alpha * (A @ B) + beta * Dm
+        C = _emulated_ab(lib, A, B, Dm, alpha, beta)
+    assert np.isposinf(C[11, 50].real)
+    assert np.array_equal(C[7], beta * Dm[7]) and np.array_equal(C[:, 40], beta * Dm[:, 40])
+    fin = np.isfinite(ref)
+    scale = np.abs(A) @ np.abs(B) + np.abs(Dm)
+    assert np.max(np.abs(C[fin] - ref[fin]) / scale[fin]) <= 1e-13
+    assert np.max(np.abs(C[3, :8] - ref[3, :8]) / np.abs(ref[3, :8])) <= 2.0 ** -52
