@@ -74,6 +74,7 @@ constexpr int OZ_DRAIN_WARPS = 16;     // four per TMEM lane quadrant
 constexpr int OZ_DCOLS = OZ_BN / (OZ_DRAIN_WARPS / 4);   // columns of exact state per drain thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;
 constexpr int OZP_THREADS = 256;
+constexpr int OZ_EG = 2;                 // output columns per group of epilogue loads
 
 static_assert(OZ_NBUF * OZ_ACC <= (int)OZ_TMEM_COLS, "accumulators exceed tensor memory");
 static_assert((long long)OZ_S * OZ_TMAX * OZ_TMAX * OZ_DRAIN * OZ_BK < (1ll << 24), "FP32 accumulation not exact");
@@ -544,6 +545,17 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        if (c == last && in_row) {   // the epilogue's operands into L1 while the last chunk drains
+          const c64* dp = use_d ? D + (int64_t)row * P.ldd + col0 : nullptr;
+          const double* sp = scales + e * scale_es + P.sb + col0;
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(scales + e * scale_es + P.sa + row));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(sp));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(sp + OZ_DCOLS - 1));
+          if (dp) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(dp));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(dp + OZ_DCOLS - 1));
+          }
+        }
         // real product v of the chunk: T0 adds to Re and subtracts from Im, T1 subtracts from both,
         // T2 adds to Im (each chunk value negated first for a negative alpha on the integer path)
         const int v = c / it.nchunk;
@@ -606,17 +618,30 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           // takes the FP64 path, as do a D beyond 2^31 sigma_i tau_j and a non-finite D
           const int er2 = oz_expo(scales[e * scale_es + P.sa + row]);
           const double* scn = scales + e * scale_es + P.sb + col0;
+          // in groups of 4 columns, every load of a group before any store: the compiler must assume
+          // that C aliases D and the scales, so loads interleaved with the stores would be one
+          // memory round trip per column
 #pragma unroll
-          for (int j = 0; j < OZ_DCOLS; ++j) {
-            if (col0 + j < P.N) {
-              const int ecj = oz_expo(scn[j]);
-              const int es = er2 - 1023 - 63 + ecj - 1023 + (iep ? ka : 0);
-              bool f = !iep || er2 == 0 || ecj == 0;
+          for (int j0 = 0; j0 < OZ_DCOLS; j0 += OZ_EG) {
+            int ecs[OZ_EG];
+            c64 dvs[OZ_EG];
+#pragma unroll
+            for (int q = 0; q < OZ_EG; ++q) {
+              const bool in = col0 + j0 + q < P.N;
+              ecs[q] = in ? oz_expo(scn[j0 + q]) : 0;
+              dvs[q] = (in && use_d) ? drow[j0 + q] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int q = 0; q < OZ_EG; ++q) {
+              const int j = j0 + q;
+              if (col0 + j >= P.N) continue;
+              const int es = er2 - 1023 - 63 + ecs[q] - 1023 + (iep ? ka : 0);
+              bool f = !iep || er2 == 0 || ecs[q] == 0;
               if (!f && use_d) {   // fold beta D / 2^ka into the sums
-                const c64 d = drow[j];
                 long long h0, h1;
                 unsigned int l0, l1;
-                f = !oz_double_to_fix(d.x, es - kb, bneg, h0, l0) || !oz_double_to_fix(d.y, es - kb, bneg, h1, l1);
+                f = !oz_double_to_fix(dvs[q].x, es - kb, bneg, h0, l0) ||
+                    !oz_double_to_fix(dvs[q].y, es - kb, bneg, h1, l1);
                 if (!f) {
                   unsigned int ln = Lr[j] + l0;
                   Hr[j] += h0 + (ln < l0 ? 1 : 0);
@@ -633,7 +658,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
                 if (!iep) o = real_ab ? make_double2(g.ar * xr, g.ar * xi)
                                       : make_double2(g.ar * xr - g.ai * xi, g.ar * xi + g.ai * xr);
                 if (use_d) {
-                  const c64 d = drow[j];
+                  const c64 d = dvs[q];
                   if (real_ab) {
                     o.x = fma(g.br, d.x, o.x);
                     o.y = fma(g.br, d.y, o.y);
