@@ -17,6 +17,7 @@ sub-grids), no data-path collective; value = energies of all ranks / max-over-ra
 (weak scaling).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -28,6 +29,11 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# DRAM traffic of the FP64-emulation GEMM class (k_gemm_oz + k_oz_pack), per class launch, from one
+# ncu launch list of the metric workload (dram__bytes_read.sum + dram__bytes_write.sum; the command
+# and table are in profiles/launches_cubic32x64E_fp64.md). Valid only for the kernel source it was
+# taken on: bench.py reports null once csrc/gemm_oz.cu differs from that source.
+OZ_TRAFFIC = {"gemm_oz_sha256": None, "bytes_per_class_launch": None, "launches_per_solve": None}
 sys.path.insert(0, ROOT)
 
 METRIC = "energy pts/s for diag(G^r,G^<) on 32^3 grid"
@@ -309,11 +315,17 @@ def run_hsc(args):
     # FP64 emulation: 36 slice products x 3 real products x 2 flops per complex MAC = 27 x the
     # 8-flop complex count, executed as BF16 MMAs
     oz_bf16 = 27.0 * rate(go)
+    src = os.path.join(ROOT, "paper_1702_05167_gb300", "csrc", "gemm_oz.cu")
+    same_src = os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == OZ_TRAFFIC["gemm_oz_sha256"]
     emul = {"kernel": "k_gemm_oz (+k_oz_pack): complex128 GEMM emulated on the BF16 tensor cores "
-                      "(tcgen05.mma kind::f16, 8 exact 7-bit slices per operand, FP32 TMEM "
-                      "accumulators drained to FP64 every 128 K values)", "bound": "tensor",
+                      "(tcgen05.mma kind::f16, 8 balanced base-128 digits per operand, FP32 TMEM "
+                      "accumulators drained every 384 K values into exact 96-bit integer sums, one "
+                      "rounding per output)", "bound": "tensor",
             "achieved": oz_bf16, "peak": bf16_sust, "unit": "TFLOP/s", "frac": oz_bf16 / bf16_sust,
-            "traffic": None,
+            "traffic": OZ_TRAFFIC["bytes_per_class_launch"] if same_src else None,
+            "traffic_unit": "bytes per class launch (k_gemm_oz + k_oz_pack, ncu dram__bytes_read.sum + "
+                            "dram__bytes_write.sum, averaged over one solve's launches)",
+            "traffic_note": None if same_src else "kernel source changed since the counters were taken",
             "flop_convention": "BF16 MMA flops the scheme needs: 36 slice pairs x 3 real products x "
                                "2 M N K per complex GEMM (27 x the 8-flop complex count), no padding",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",

@@ -202,6 +202,12 @@ __device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// two FP32 values as one word of two BF16 (round to nearest even; a in the low half)
+__device__ __forceinline__ uint32_t oz_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 __device__ __forceinline__ int oz_expo(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
@@ -299,36 +305,41 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
         const long long mag = (ex > 0 && shift < 64) ? (long long)(shift >= 0 ? mant >> shift : mant << (-shift)) : 0ll;
         m[q] = (bits >> 63) ? -mag : mag;
       }
-      // balanced base-128 digits, least significant first: t = ((m + 64) mod 128) - 64, m = (m - t) / 128
-      int dg[OZ_S][8];
+      // balanced base-128 digits, least significant first: t = ((m + 64) mod 128) - 64, m = (m - t) / 128,
+      // in 32-bit halves: the low 28 bits m mod 2^28 give digits 7..4 and a carry (0 or 1) into
+      // the high part floor(m / 2^28) (|.| < 2^27), which gives digits 3..1 and the leading digit.
+      // A digit t becomes FP32 through the bit pattern of 1.5 2^23 + t (unit spacing there: exact
+      // for |t| < 2^22), and two of them become one word of two BF16 (exact: |t| <= 65 has 7 bits).
+      uint32_t wd[OZ_S][4];   // slice sl, k pair p: the BF16 digits of k0 + 2p and k0 + 2p + 1
 #pragma unroll
-      for (int sl = OZ_S - 1; sl > 0; --sl)
+      for (int p = 0; p < 4; ++p) {
+        float f[2][OZ_S];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int t = (int)((m[q] + 64) & 127) - 64;
-          dg[sl][q] = t;
-          m[q] = (m[q] - t) >> 7;   // exact: m - t is a multiple of 128
+        for (int h = 0; h < 2; ++h) {
+          const long long mq = m[2 * p + h];
+          int lo = (int)(mq & ((1ll << 28) - 1));
+          int hi = (int)(mq >> 28);
+#pragma unroll
+          for (int sl = OZ_S - 1; sl >= OZ_S - 4; --sl) {
+            const int t = ((lo + 64) & 127) - 64;
+            f[h][sl] = __int_as_float(0x4B400000 + t) - 12582912.0f;
+            lo = (lo - t) >> 7;   // exact: lo - t is a multiple of 128
+          }
+          hi += lo;
+#pragma unroll
+          for (int sl = OZ_S - 5; sl > 0; --sl) {
+            const int t = ((hi + 64) & 127) - 64;
+            f[h][sl] = __int_as_float(0x4B400000 + t) - 12582912.0f;
+            hi = (hi - t) >> 7;
+          }
+          f[h][0] = __int_as_float(0x4B400000 + hi) - 12582912.0f;   // the leading digit, |t| <= 65
         }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) dg[0][q] = (int)m[q];   // the leading digit, |t| <= 65
-#pragma unroll
-      for (int sl = 0; sl < OZ_S; ++sl) {
-        uint32_t h[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int t = dg[sl][q];
-          const uint32_t tq = (uint32_t)(t < 0 ? -t : t);
-          // |t| as an FP32 value (exact: |t| < 2^23), whose upper half is its exact BF16 encoding
-          const float f = __uint_as_float(0x4B000000u | tq) - 8388608.0f;
-          h[q] = (__float_as_uint(f) >> 16) | (t < 0 ? 0x8000u : 0u);
-        }
-        uint4 w;
-        w.x = h[0] | (h[1] << 16);
-        w.y = h[2] | (h[3] << 16);
-        w.z = h[4] | (h[5] << 16);
-        w.w = h[6] | (h[7] << 16);
-        *reinterpret_cast<uint4*>(o + v * vstride + sl * (rows * OZ_BK)) = w;
+        for (int sl = 0; sl < OZ_S; ++sl) wd[sl][p] = oz_bf16x2(f[0][sl], f[1][sl]);
       }
+#pragma unroll
+      for (int sl = 0; sl < OZ_S; ++sl)
+        *reinterpret_cast<uint4*>(o + v * vstride + sl * (rows * OZ_BK)) = make_uint4(wd[sl][0], wd[sl][1], wd[sl][2], wd[sl][3]);
     }
   }
 }
