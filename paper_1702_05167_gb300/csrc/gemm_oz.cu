@@ -13,7 +13,8 @@
 //     written in balanced base-128 digits: X_ik = sigma_i (sum_s t_s 2^(-7 s) + delta), |delta| <
 //     2^-56, with OZ_S = 8 digits t_s in [-64, 63] (the leading one in [-65, 65]), each exact in
 //     BF16; the slicing works on the FP64 bit pattern (integer operations only: GB300's FP64 pipe is
-//     slow);
+//     slow); the fixed-point value of Ar + Ai is the exact sum of those of Ar and Ai (|delta| <
+//     2^-55), so T2 - T0 - T1 is exactly the cross term of the truncated operands;
 //   * a digit product t_s u_r has |t_s u_r| <= 65^2 and carries the weight 2^(-7 (s + r)); the
 //     products of one diagonal d = s + r (d <= OZ_S + 1: 36 pairs) accumulate in one FP32 tensor-
 //     memory accumulator, exact for 384 K values (at most 8 pairs: 8 * 65^2 * 384 < 2^24); every
@@ -290,12 +291,15 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = load(r, k0 + q);
     uint16_t* o = dst + (int64_t)(k0 / OZ_BK) * blkv + oz_cidx(r, k0 % OZ_BK);
+    // the fixed-point values of re and im; that of re + im is their exact sum, so that the three
+    // real operands satisfy A2 = A0 + A1 exactly (|A0 + A1| < 2^55 + 2: the row's scale covers
+    // re + im, and each truncation is below one unit)
+    long long m01[2][8];
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      long long m[8];
+    for (int v = 0; v < 2; ++v)
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const double val = v == 0 ? x[q].x : (v == 1 ? x[q].y : x[q].x + x[q].y);
+        const double val = v == 0 ? x[q].x : x[q].y;
         const unsigned long long bits = (unsigned long long)__double_as_longlong(val);
         const int ex = (int)((bits >> 52) & 0x7FF);
         // floor(|x| / sigma * 2^56) < 2^55: |x| = mant 2^(ex - 1075), sigma = 2^(E - 1021), so the
@@ -303,8 +307,13 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
         const int shift = s_e[0][r] - ex + (52 - OZ_FRAC + 2);
         const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
         const long long mag = (ex > 0 && shift < 64) ? (long long)(shift >= 0 ? mant >> shift : mant << (-shift)) : 0ll;
-        m[q] = (bits >> 63) ? -mag : mag;
+        m01[v][q] = (bits >> 63) ? -mag : mag;
       }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      long long m[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) m[q] = v < 2 ? m01[v][q] : m01[0][q] + m01[1][q];
       // balanced base-128 digits, least significant first: t = ((m + 64) mod 128) - 64, m = (m - t) / 128,
       // in 32-bit halves: the low 28 bits m mod 2^28 give digits 7..4 and a carry (0 or 1) into
       // the high part floor(m / 2^28) (|.| < 2^27), which gives digits 3..1 and the leading digit.
