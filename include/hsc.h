@@ -231,6 +231,15 @@ typedef enum {
                               /* columns alone their products update; one trailing product with */
                               /* K = this width then updates the rest of the block (default 128; */
                               /* 0 or <= the panel width: every panel updates the whole block)   */
+  HSC_OPT_LEAF_BAND = 13,     /* 1 (default): the downward products of a leaf cluster (no       */
+                              /* children) form G_ii and G^<_ii only on the column band of each */
+                              /* block of <= 128 rows that spans the entries read afterwards:   */
+                              /* the diagonal, the H neighbours the residual check reads (G^r), */
+                              /* requested pairs inside the block, and (lesser leaves) every    */
+                              /* column of G_ii's contact rows; other entries of those blocks   */
+                              /* are left undefined. A solve whose requested pairs fall in a    */
+                              /* leaf block outside the current bands rebuilds the schedule     */
+                              /* first. 0: the whole blocks (identical computed entries)        */
   HSC_OPT_TREE_FORM = 11      /* read only: the tree of the last hsc_analyze: 0 plain geometric,*/
                               /* 1 contact-connected geometric, 2 graph bisection (-1 before    */
                               /* any analysis). With HSC_OPT_ORDERING = 0 the contact-connected */

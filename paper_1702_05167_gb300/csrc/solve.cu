@@ -12,6 +12,7 @@
 //   downward  G_iU = -X G_UU;  G_ii = D^{-1} - X G_iU^T                        (Algorithm 1)
 //             W = D^{-1} [L_ii conj(G_ii) + L_iU conj(G_Ui) | L_ii conj(G_iU) + L_iU conj(G_UU)]
 //             P_iU = W_iU - X P_UU;  P_ii = W_ii + X P_iU^dagger              (Algorithm 2)
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -481,6 +482,88 @@ int build_schedule(hsc_ctx* h) {
     }
   }
 
+  // residual check: location of G_uv for every non-zero (u, v) (also the leaf bands below)
+  std::vector<int64_t> rloc(h->col.size());
+  for (int64_t u = 0; u < P.n; ++u)
+    for (int64_t k = h->rowptr[u]; k < h->rowptr[u + 1]; ++k) {
+      int64_t off = 0;
+      if (!locate_pair(P, u, h->col[k], &off))
+        return hsc_fail(h, HSC_ERR_ARG, "an H entry lies outside the selected pattern");
+      rloc[k] = off >= 0 ? off : -off - 1;   // G^r is complex symmetric
+    }
+
+  // Leaf clusters (no children) are nobody's ancestors, so their diagonal blocks G_ii and G^<_ii
+  // are read afterwards only at: the diagonal (outputs), the H neighbours of the residual check
+  // (G^r), requested pairs inside the block, and, on a lesser leaf, every column of G_ii's contact
+  // rows [c0, c1) (the lesser products). Per leaf and row, the first and last column read.
+  const bool band = h->opt_leaf_band != 0;
+  std::vector<std::vector<int>> gmin(nc), gmax(nc), pmin(nc), pmax(nc);
+  std::vector<std::pair<int64_t, int>> aug_start;   // (block start, leaf)
+  if (band) {
+    for (int i = 0; i < nc; ++i) {
+      const Cluster& c = P.cl[i];
+      if (c.nchild != 0) continue;
+      gmin[i].resize(c.n); gmax[i].resize(c.n); pmin[i].resize(c.n); pmax[i].resize(c.n);
+      for (int r = 0; r < (int)c.n; ++r) gmin[i][r] = gmax[i][r] = pmin[i][r] = pmax[i][r] = r;
+      aug_start.push_back({P.off[i].aug, i});
+    }
+    std::sort(aug_start.begin(), aug_start.end());
+    // (row, column) of position p if it lies in a leaf's diagonal block
+    auto in_leaf = [&](int64_t p, int& leaf, int& r, int& col) {
+      auto it = std::upper_bound(aug_start.begin(), aug_start.end(), std::make_pair(p, nc));
+      if (it == aug_start.begin()) return false;
+      --it;
+      const Cluster& c = P.cl[it->second];
+      const int64_t w = c.n + c.m, q = p - it->first;
+      if (q < 0 || q >= c.n * w || q % w >= c.n) return false;
+      leaf = it->second;
+      r = (int)(q / w);
+      col = (int)(q % w);
+      return true;
+    };
+    int lf, r, col;
+    for (int64_t p : rloc)
+      if (in_leaf(p, lf, r, col)) {
+        gmin[lf][r] = std::min(gmin[lf][r], col);
+        gmax[lf][r] = std::max(gmax[lf][r], col);
+      }
+    for (int64_t p : h->band_pairs)
+      if (in_leaf(p, lf, r, col)) {
+        gmin[lf][r] = std::min(gmin[lf][r], col);
+        gmax[lf][r] = std::max(gmax[lf][r], col);
+        pmin[lf][r] = std::min(pmin[lf][r], col);
+        pmax[lf][r] = std::max(pmax[lf][r], col);
+      }
+  }
+  // Rows [r0, r1) of a leaf's block per product: segments of <= 128 rows (cut also at c0 and c1
+  // when whole contact rows are read), each with the column span [lo, hi) of the entries read.
+  struct Band { int r0, r1, lo, hi; };
+  auto bands = [&](int i, bool g) {
+    std::vector<Band> out;
+    const int n = (int)P.cl[i].n;
+    const bool rows_whole = g && P.cl[i].lesser;   // lesser leaf: contact rows of G_ii entire
+    const int c0 = rows_whole ? hc0[i] : n, c1 = rows_whole ? hc1[i] : n;
+    const auto& mn = g ? gmin[i] : pmin[i];
+    const auto& mx = g ? gmax[i] : pmax[i];
+    int r0 = 0;
+    while (r0 < n) {
+      int r1 = std::min(n, r0 + 128);
+      if (r0 < c0 && r1 > c0) r1 = c0;
+      if (r0 >= c0 && r0 < c1) r1 = std::min(r1, c1);
+      int lo = n, hi = 0;
+      if (r0 >= c0 && r0 < c1) { lo = 0; hi = n; }
+      else
+        for (int r = r0; r < r1; ++r) { lo = std::min(lo, mn[r]); hi = std::max(hi, mx[r] + 1); }
+      out.push_back(Band{r0, r1, lo, hi});
+      r0 = r1;
+    }
+    return out;
+  };
+  // a lesser leaf without contact rows of its own reads its whole G_ii block (general lesser path)
+  auto banded = [&](int i, bool g) {
+    return band && P.cl[i].nchild == 0 && !(g && P.cl[i].lesser && !leafl[i]);
+  };
+
   // downward levels
   d->down.assign(P.by_depth.size(), DownLevel());
   for (size_t dl = 0; dl < P.by_depth.size(); ++dl) {
@@ -511,7 +594,13 @@ int build_schedule(hsc_ctx* h) {
     GemmList g2(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      g2.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, 1);
+      const int64_t w = L.n + L.m;
+      if (banded(ids[k], true))
+        for (const Band& b : bands(ids[k], true))
+          g2.add(b.r1 - b.r0, b.hi - b.lo, L.m, L.x + (int64_t)b.r0 * L.m, L.m, L.aug + L.n + b.lo * w, w,
+                 L.aug + b.r0 * w + b.lo, w, L.aug + b.r0 * w + b.lo, w, 1);
+      else
+        g2.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, w, L.aug, w, L.aug, w, 1);
     }
     D.d[1] = g2.args(OP_N, OP_T, -1, 0, 1, 0);
     GemmList g3(gps, gps128, gpsoz);
@@ -557,7 +646,12 @@ int build_schedule(hsc_ctx* h) {
       const auto& L = lv[k];
       const int i = ids[k], c0 = hc0[i], w = hc1[i] - hc0[i];
       if (!L.lesser) continue;
-      if (leafl[i])   // W = D^{-1}[:, c0:c1) N[c0:c1, :]
+      if (leafl[i] && banded(i, false)) {   // W = D^{-1}[:, c0:c1) N[c0:c1, :]: W_iU whole, W_ii banded
+        const int64_t ld = L.n + L.m, nro = L.tn + (int64_t)c0 * ld;
+        g7.add(L.n, L.m, w, L.aug + c0, ld, nro + L.n, ld, L.aug + L.n, ld);
+        for (const Band& b : bands(i, false))
+          g7.add(b.r1 - b.r0, b.hi - b.lo, w, L.aug + b.r0 * ld + c0, ld, nro + b.lo, ld, L.aug + b.r0 * ld + b.lo, ld);
+      } else if (leafl[i])
         g7.add(L.n, L.n + L.m, w, L.aug + c0, L.n + L.m, L.tn + (int64_t)c0 * (L.n + L.m), L.n + L.m, L.aug,
                L.n + L.m);
       else
@@ -573,7 +667,13 @@ int build_schedule(hsc_ctx* h) {
     GemmList g9(gps, gps128, gpsoz);
     for (int k = 0; k < D.nl; ++k) {
       const auto& L = lv[k];
-      g9.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, L.n + L.m, L.aug, L.n + L.m, L.aug, L.n + L.m, L.lesser);
+      const int64_t w = L.n + L.m;
+      if (banded(ids[k], false))
+        for (const Band& b : bands(ids[k], false))
+          g9.add(b.r1 - b.r0, b.hi - b.lo, L.m, L.x + (int64_t)b.r0 * L.m, L.m, L.aug + L.n + b.lo * w, w,
+                 L.aug + b.r0 * w + b.lo, w, L.aug + b.r0 * w + b.lo, w, L.lesser);
+      else
+        g9.add(L.n, L.n, L.m, L.x, L.m, L.aug + L.n, w, L.aug, w, L.aug, w, L.lesser);
     }
     D.d[8] = g9.args(OP_N, OP_H, 1, 0, 1, 0);
   }
@@ -613,15 +713,7 @@ int build_schedule(hsc_ctx* h) {
   }
   std::vector<c64> hv(h->val.size());
   for (size_t k = 0; k < hv.size(); ++k) hv[k] = make_double2(h->val[k].re, h->val[k].im);
-  // residual check: location of G_uv for every non-zero (u, v), contact slot of every unknown
-  std::vector<int64_t> rloc(h->col.size());
-  for (int64_t u = 0; u < P.n; ++u)
-    for (int64_t k = h->rowptr[u]; k < h->rowptr[u + 1]; ++k) {
-      int64_t off = 0;
-      if (!locate_pair(P, u, h->col[k], &off))
-        return hsc_fail(h, HSC_ERR_ARG, "an H entry lies outside the selected pattern");
-      rloc[k] = off >= 0 ? off : -off - 1;   // G^r is complex symmetric
-    }
+  // contact slot of every unknown (residual check)
   std::vector<int32_t> uslot(P.n, -1);
   for (int64_t u = 0; u < P.n; ++u)
     uslot[u] = P.own_contact[P.own_off[P.unk_cluster[u]] + P.unk_local[u]];
@@ -1034,15 +1126,29 @@ int check_common(hsc_ctx* h, int64_t n_E, const double* E, double eta, const hsc
 
 // Locates the requested pairs and copies their source offsets into a persistent device buffer.
 int upload_pairs(hsc_ctx* h, int32_t n_req, const int32_t* req_pairs) {
-  DeviceState* d = h->dev;
   std::vector<int64_t> poff(n_req);
+  std::vector<int64_t> in_leaf;   // positions of the pairs inside a leaf's diagonal block
   for (int k = 0; k < n_req; ++k) {
     int64_t a = req_pairs[2 * k], b = req_pairs[2 * k + 1];
     if (a < 0 || a >= h->n || b < 0 || b >= h->n) return hsc_fail(h, HSC_ERR_ARG, "pair index out of range");
     if (!locate_pair(h->plan, a, b, &poff[k]))
       return hsc_fail(h, HSC_ERR_NOT_SELECTED, "pair (" + std::to_string(a) + "," + std::to_string(b) +
                                                    ") is outside the filled pattern");
+    const int ca = h->plan.unk_cluster[a];
+    if (ca == h->plan.unk_cluster[b] && h->plan.cl[ca].nchild == 0)
+      in_leaf.push_back(poff[k] >= 0 ? poff[k] : -poff[k] - 1);
   }
+  std::sort(in_leaf.begin(), in_leaf.end());
+  in_leaf.erase(std::unique(in_leaf.begin(), in_leaf.end()), in_leaf.end());
+  if (h->opt_leaf_band && in_leaf != h->band_pairs) {
+    // the leaves' column bands must cover these entries: rebuild the schedule with them
+    h->band_pairs = in_leaf;
+    device_state_free(h->dev);
+    h->dev = nullptr;
+    int rc = get_state(h);
+    if (rc != HSC_OK) return rc;
+  }
+  DeviceState* d = h->dev;
   if (n_req > d->pair_cap) {
     if (d->poff) cudaFree(d->poff);
     d->poff = nullptr;
