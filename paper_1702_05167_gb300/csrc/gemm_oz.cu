@@ -4,7 +4,10 @@
 // Algorithms 59, 2012).
 //
 // C = alpha op(A) op(B) + beta D. The complex product is taken as three real products (3M):
-//     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),   AB = (T0 - T1) + i (T2 - T0 - T1).
+//     T0 = Ar Br,  T1 = Ai Bi,  T2 = (Ar + Ai)(Br + Bi),   AB = (T0 - T1) + i (T2 - T0 - T1);
+// for K <= 192 as four, Re = Ar Br + (-Ai) Bi and Im = Ar Bi + Ai Br, each accumulated whole in one
+// set of tensor-memory accumulators (two drains per output tile instead of three: there the drain,
+// not the tensor pipe, bounds the kernel).
 // Each real product X Y (X: M x K, Y: K x N) is evaluated exactly up to a bounded truncation:
 //   * row i of the three real operands Ar, Ai, Ar + Ai gets one power of two sigma_i > 2 max |.|
 //     over the row (columns j of Br, Bi, Br + Bi likewise tau_j), so that the three products are
@@ -66,6 +69,8 @@ constexpr int OZ_ABLK = OZ_S * OZ_BM * OZ_BK;   // bf16 values of one A block (a
 constexpr int OZ_BBLK = OZ_S * OZ_BN * OZ_BK;
 constexpr int OZ_STAGES = 5;
 constexpr int OZ_DRAIN = 24;             // K steps per drain (384 K values)
+constexpr int OZ_M4_KS = 12;             // K steps up to which a product takes four real products:
+                                         // Re and Im each accumulated whole (2 x 192 K values)
 constexpr int OZ_TMAX = 65;              // largest |digit|
 constexpr int OZ_ACC = OZ_ND * OZ_BN;     // TMEM columns of one set of accumulators
 constexpr uint32_t OZ_TMEM_COLS = 512;
@@ -239,6 +244,9 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
   const int row0 = tile * rows;
   const int nrow = isA ? P.M : P.N;
   const int K = P.K, ks = P.ksteps;
+  // products of up to OZ_M4_KS K steps take four real products: no Ar + Ai operand
+  const bool m4 = ks <= OZ_M4_KS;
+  const int nv = m4 ? 2 : 3;
   const c64* X = reinterpret_cast<const c64*>(isA ? g.A : g.B) + e * (isA ? g.a_es : g.b_es) + (isA ? P.a : P.b);
   const int ld = isA ? P.lda : P.ldb;
   // row r of op(A) (or of op(B)^T) is contiguous in memory for op(A) in {N, C} and op(B) in {T, H}
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
       const c64 x = load(r, k0 + q);
       e0 = max(e0, oz_expo(x.x));
       e1 = max(e1, oz_expo(x.y));
-      e2 = max(e2, oz_expo(x.x + x.y));
+      if (!m4) e2 = max(e2, oz_expo(x.x + x.y));
     }
     // one scale per row for all three real operands, so that their products are exact integers in
     // the same units and the complex result can be combined before any rounding
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(OZP_THREADS) k_oz_pack(GemmArgs g, uint16_t* s
         m01[v][q] = (bits >> 63) ? -mag : mag;
       }
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
+    for (int v = 0; v < nv; ++v) {
       long long m[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) m[q] = v < 2 ? m01[v][q] : m01[0][q] + m01[1][q];
@@ -390,7 +398,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
   // problems' first tiles)
   struct Item {
     GemmProb P;
-    int e, tm, tn, ks, nchunk;
+    int e, tm, tn, ks, nchunk, m4, nch, nst;
   };
   auto item = [&](int idx) {
     Item it;
@@ -408,6 +416,11 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
     it.tn = t % it.P.tiles_n;
     it.ks = it.P.ksteps;
     it.nchunk = (it.ks + OZ_DRAIN - 1) / OZ_DRAIN;   // per real product
+    // K <= 192: four real products, Re = ArBr + (-Ai)Bi and Im = ArBi + AiBr accumulated in one
+    // chunk each (2 drains per tile instead of 3); larger K: three (3M), a chunk per 384 K values
+    it.m4 = it.ks > 0 && it.ks <= OZ_M4_KS;
+    it.nch = it.m4 ? 2 : 3 * it.nchunk;
+    it.nst = it.m4 ? 4 * it.ks : 3 * it.ks;
     return it;
   };
 
@@ -445,7 +458,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
         const Item it = item(idx);
         const uint16_t* sl = slices + it.e * slice_es;
-        for (int s = 0; s < 3 * it.ks; ++s, ++sg) {
+        for (int s = 0; s < it.nst; ++s, ++sg) {
           const int st = sg % OZ_STAGES;
           if (sg >= OZ_STAGES && !oz_wait(oz_su32(&sm.empty[st]), (uint32_t)((sg / OZ_STAGES - 1) & 1))) {
             atomicExch(flag, 3);
@@ -453,9 +466,11 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
             ok = false;
             break;
           }
-          const int v = s / it.ks, kk = s % it.ks;
-          const uint16_t* pa = sl + it.P.pa + (((int64_t)v * it.P.tiles_m + it.tm) * it.ks + kk) * OZ_ABLK;
-          const uint16_t* pb = sl + it.P.pb + (((int64_t)v * it.P.tiles_n + it.tn) * it.ks + kk) * OZ_BBLK;
+          // operand pair of the stage: 3M (v, v); four products (re, re), (im, im), (re, im), (im, re)
+          const int q = s / it.ks, kk = s % it.ks;
+          const int va = it.m4 ? (q & 1) : q, vb = it.m4 ? (q == 1 || q == 2) : q;
+          const uint16_t* pa = sl + it.P.pa + (((int64_t)va * it.P.tiles_m + it.tm) * it.ks + kk) * OZ_ABLK;
+          const uint16_t* pb = sl + it.P.pb + (((int64_t)vb * it.P.tiles_n + it.tn) * it.ks + kk) * OZ_BBLK;
           const uint32_t fb = oz_su32(&sm.full[st]);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ABYTES + BBYTES)
                        : "memory");
@@ -470,7 +485,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       bool ok = true;
       for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
         const Item it = item(idx);
-        for (int c = 0; c < 3 * it.nchunk && ok; ++c, ++cg) {
+        for (int c = 0; c < it.nch && ok; ++c, ++cg) {
           const int ab = cg % OZ_NBUF;   // accumulator set of this chunk; its previous use was cg - OZ_NBUF
           if (cg >= OZ_NBUF && !oz_wait(oz_su32(&sm.acc_empty[ab]), (uint32_t)((cg / OZ_NBUF - 1) & 1))) {
             atomicExch(flag, 3);
@@ -480,7 +495,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const int v = c / it.nchunk, cc = c % it.nchunk;
-          const int s0 = v * it.ks + cc * OZ_DRAIN, s1 = v * it.ks + min(it.ks, (cc + 1) * OZ_DRAIN);
+          const int s0 = it.m4 ? 2 * c * it.ks : v * it.ks + cc * OZ_DRAIN;
+          const int s1 = it.m4 ? s0 + 2 * it.ks : v * it.ks + min(it.ks, (cc + 1) * OZ_DRAIN);
           for (int s = s0; s < s1; ++s, ++sg) {
             const int st = sg % OZ_STAGES;
             if (!oz_wait(oz_su32(&sm.full[st]), (uint32_t)((sg / OZ_STAGES) & 1))) {
@@ -496,11 +512,13 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
             // its column block r lands in the accumulator of diagonal s + r, which starts at TMEM
             // column 32 (s + r - 2). 8 MMAs per K step instead of 36, the same products.
 #pragma unroll
+            // (-Ai) Bi of Re: the instruction descriptor's negate-A bit (BF16 negation is exact)
+            const uint32_t neg = (it.m4 && c == 0 && s >= s0 + it.ks) ? (1u << 13) : 0u;
             for (int si = 0; si < OZ_S; ++si) {
               // the first MMA of a chunk (si = 0) covers every diagonal and starts the accumulation
               const uint32_t acc = (s > s0 || si > 0) ? 1u : 0u;
               oz_mma(tmem + ab * OZ_ACC + si * OZ_BN, oz_desc(a0 + si * (OZ_BM * OZ_BK * 2)), oz_desc(b0),
-                     idesc_n(OZ_S - si), acc);
+                     idesc_n(OZ_S - si) | neg, acc);
             }
             oz_commit(oz_su32(&sm.empty[st]));
           }
@@ -531,7 +549,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       const bool use_d = D != nullptr && P.use_d && (g.br != 0.0 || g.bi != 0.0) && !(row >= P.zr0 && row < P.zr1);
       const int col0 = it.tn * OZ_BN + part * OZ_DCOLS;
       const bool in_row = row < P.M;
-      const int last = 3 * it.nchunk - 1;
+      const int last = it.nch - 1;
       if (it.ks == 0 && in_row) {   // C = beta D
         for (int j = 0; j < OZ_DCOLS && col0 + j < P.N; ++j) {
           c64 o = make_double2(0.0, 0.0);
@@ -551,7 +569,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
       unsigned int Lr[OZ_DCOLS], Li[OZ_DCOLS];
 #pragma unroll
       for (int j = 0; j < OZ_DCOLS; ++j) { Hr[j] = 0; Hi[j] = 0; Lr[j] = 0u; Li[j] = 0u; }
-      for (int c = 0; c < 3 * it.nchunk; ++c, ++cg) {
+      for (int c = 0; c < it.nch; ++c, ++cg) {
         const int ab = cg % OZ_NBUF;
         bool got = oz_wait(oz_su32(&sm.acc_full[ab]), (uint32_t)((cg / OZ_NBUF) & 1));
         got = __all_sync(0xffffffffu, got);   // warp-uniform before the .sync.aligned TMEM loads
@@ -578,7 +596,7 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
         }
         // real product v of the chunk: T0 adds to Re and subtracts from Im, T1 subtracts from both,
         // T2 adds to Im (each chunk value negated first for a negative alpha on the integer path)
-        const int v = c / it.nchunk;
+        const int v = it.m4 ? 3 + c : c / it.nchunk;   // 3M products 0..2; four products: Re 3, Im 4
 #pragma unroll
         for (int c0 = 0; c0 < OZ_DCOLS; c0 += 2) {
           // all 8 diagonals of 2 columns behind one wait
@@ -607,20 +625,20 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
               lc = 0u - lc;
             }
             const int q = c0 + j;
-            if (v == 0) {        // Re += T0
+            if (v == 0 || v == 3) {   // Re += T0, Re += the four-product Re
               const unsigned int ln = Lr[q] + lc;
               Hr[q] += hc + (ln < lc ? 1 : 0);
               Lr[q] = ln;
-            } else if (v == 1) { // Re -= T1
+            } else if (v == 1) {      // Re -= T1
               const unsigned int ln = Lr[q] - lc;
               Hr[q] -= hc + (Lr[q] < lc ? 1 : 0);
               Lr[q] = ln;
             }
-            if (v == 2) {        // Im += T2
+            if (v == 2 || v == 4) {   // Im += T2, Im += the four-product Im
               const unsigned int ln = Li[q] + lc;
               Hi[q] += hc + (ln < lc ? 1 : 0);
               Li[q] = ln;
-            } else {             // Im -= T0, Im -= T1
+            } else if (v <= 1) {      // Im -= T0, Im -= T1
               const unsigned int ln = Li[q] - lc;
               Hi[q] -= hc + (Li[q] < lc ? 1 : 0);
               Li[q] = ln;

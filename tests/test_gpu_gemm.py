@@ -153,16 +153,18 @@ def _scheme_scales(X, axis):
     return np.where(m > 0, 2.0 ** (np.floor(np.log2(np.where(m > 0, m, 1))) + 2), 0.0)
 
 
-def test_fp64_emulation_within_row_dynamic_range(lib):
+@pytest.mark.parametrize("K", [128, 700])
+def test_fp64_emulation_within_row_dynamic_range(lib, K):
     """Entries of one row of A (and of one column of B) spanning 2^-40 .. 1: the emulation keeps 56
     bits relative to each row's and column's scale (sigma_i, tau_j: powers of two above twice the
     row's or column's largest real or imaginary part), so per K value and real product its error is
     below 2^-54.5 sigma_i tau_j, and the imaginary part of the complex product carries three real
     products: |C - AB| <= 3 K 2^-54.5 sigma_i tau_j plus the final rounding (the documented bound;
     a componentwise K u |A||B| bound does not hold for entries far below their row's maximum,
-    which keep fewer bits)."""
+    which keep fewer bits). K = 128 runs the four-product form (two real products per part, the
+    scales from re and im alone, at most those of the three-product form), K = 700 the 3M form."""
     rng = np.random.default_rng(11)
-    M, N, K = 96, 80, 700
+    M, N = 96, 80
     mag = lambda *sh: 2.0 ** rng.uniform(-40, 0, sh)
     A = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * mag(M, K)
     B = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * mag(K, N)
