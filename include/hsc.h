@@ -240,6 +240,11 @@ typedef enum {
                               /* are left undefined. A solve whose requested pairs fall in a    */
                               /* leaf block outside the current bands rebuilds the schedule     */
                               /* first. 0: the whole blocks (identical computed entries)        */
+  HSC_OPT_LEAF_SPARSE = 14,   /* 1 (default): a leaf cluster's front holds no children's Schur   */
+                              /* complements, so its coupling block A_iU is the H entries alone:*/
+                              /* X = D^{-1} A_iU and the Schur update A_iU^T X are formed as     */
+                              /* gathers over that pattern in FP64 (the dense products' other   */
+                              /* terms are exact zeros). 0: dense block products                */
   HSC_OPT_TREE_FORM = 11      /* read only: the tree of the last hsc_analyze: 0 plain geometric,*/
                               /* 1 contact-connected geometric, 2 graph bisection (-1 before    */
                               /* any analysis). With HSC_OPT_ORDERING = 0 the contact-connected */

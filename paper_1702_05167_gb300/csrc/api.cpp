@@ -252,6 +252,10 @@ extern "C" int hsc_set_option(hsc_t h, int32_t option, int32_t value) {
       if (value < 0 || value > 1) return hsc_fail(h, HSC_ERR_ARG, "leaf band must be 0 or 1");
       h->opt_leaf_band = value;
       break;
+    case HSC_OPT_LEAF_SPARSE:
+      if (value < 0 || value > 1) return hsc_fail(h, HSC_ERR_ARG, "leaf sparse must be 0 or 1");
+      h->opt_leaf_sparse = value;
+      break;
     default:
       return hsc_fail(h, HSC_ERR_ARG, "unknown option");
   }
@@ -267,6 +271,7 @@ extern "C" int hsc_get_option(hsc_t h, int32_t option, int32_t* value) {
     case HSC_OPT_GJ_PANEL: *value = h->opt_nb; break;
     case HSC_OPT_GJ_WIDE: *value = h->opt_nbo; break;
     case HSC_OPT_LEAF_BAND: *value = h->opt_leaf_band; break;
+    case HSC_OPT_LEAF_SPARSE: *value = h->opt_leaf_sparse; break;
     case HSC_OPT_FP64_LEVELS: *value = h->opt_fp64_levels; break;
     case HSC_OPT_MIXED_GJ_FP64: *value = h->opt_gj_fp64; break;
     case HSC_OPT_LEAF: *value = h->leaf_max; break;
@@ -342,6 +347,7 @@ hsc_ctx* hsc_alt(hsc_ctx* h, int v) {
   a->opt_nb = h->opt_nb;
   a->opt_nbo = h->opt_nbo;
   a->opt_leaf_band = h->opt_leaf_band;
+  a->opt_leaf_sparse = h->opt_leaf_sparse;
   a->opt_fp64_levels = h->opt_fp64_levels;
   a->opt_gj_fp64 = h->opt_gj_fp64;
   a->opt_4m = h->opt_4m;

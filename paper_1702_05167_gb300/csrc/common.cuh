@@ -13,6 +13,10 @@ __host__ __device__ inline c64 cadd(c64 a, c64 b) { return make_double2(a.x + b.
 __host__ __device__ inline c64 csub(c64 a, c64 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __host__ __device__ inline c64 cconj(c64 a) { return make_double2(a.x, -a.y); }
 __host__ __device__ inline c64 cneg(c64 a) { return make_double2(-a.x, -a.y); }
+// a + f p in four fused multiply-adds
+__host__ __device__ inline c64 cfma(c64 a, c64 f, c64 p) {
+  return make_double2(fma(f.x, p.x, fma(-f.y, p.y, a.x)), fma(f.x, p.y, fma(f.y, p.x, a.y)));
+}
 // a - f p in four fused multiply-adds (two roundings per part instead of three)
 __host__ __device__ inline c64 cfms(c64 a, c64 f, c64 p) {
   return make_double2(fma(-f.x, p.x, fma(f.y, p.y, a.x)), fma(-f.x, p.y, fma(-f.y, p.x, a.y)));
@@ -88,6 +92,8 @@ struct LevelCluster {
   int64_t u0, pm0;       // update-set gather arrays
   int nseg, depth;
   int64_t elem_start;    // flattened element prefix inside the level (kernel-specific)
+  int64_t sp_cp;         // leaf with a sparse coupling block: start of its column pointers (m + 1,
+                         // absolute indices into the row list), -1 otherwise
 };
 
 // A DENSE contact's self-energy block (Section 3.1.2) and where it goes: the owner cluster's front

@@ -37,6 +37,7 @@ struct hsc_ctx {
   int opt_fp64_engine = 0;    // FP64-accurate products: 0 cost model, 1 FP64 pipe, 2 emulation
   int opt_resolve = 10;       // d: re-solve energies whose residual exceeds 10^-d (0: off)
   int opt_leaf_band = 1;      // leaves' G_ii, G^<_ii: only the column bands their readers need
+  int opt_leaf_sparse = 1;    // leaves' X and Schur products from the sparse coupling block
   std::vector<int64_t> band_pairs;   // requested pairs inside leaf blocks (positions) the current
                                      // schedule's bands cover; cleared by re-analysis
   int opt_ordering = 0;       // 0: geometric (contact-connected for end-plane contacts), 1: graph

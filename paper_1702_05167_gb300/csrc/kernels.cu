@@ -422,6 +422,56 @@ __global__ void k_gj_colperm(const GJProb* probs, c64* F, int64_t f_es, const in
   }
 }
 
+// ---- leaves: products with the sparse coupling block A_iU -------------------------------------
+// A leaf has no children, so its front's coupling block A_iU holds only the H entries between its
+// sites and U_i: column k has the few rows j coupled to U_i[k] (CSC pattern from the analysis).
+// X = D^{-1} A_iU is then a gather of D^{-1}'s columns, X[r, k] = sum_j D^{-1}[r, j] A[j, k], and the
+// Schur update S -= A_iU^T X a gather of X's rows, S[k, l] -= sum_j A[j, k] X[j, l]: the same sums as
+// the dense products (whose other terms are exact zeros), in FP64 on the CUDA cores.
+__global__ void k_leaf_x(const LevelCluster* lc, const int32_t* colptr, const int32_t* rows,
+                         const c64* F, int64_t aug_es, c64* X, int64_t x_es) {
+  const LevelCluster& C = lc[blockIdx.y];
+  const int r = blockIdx.x;
+  if (C.sp_cp < 0 || r >= C.n) return;
+  const int e = blockIdx.z;
+  const int64_t ld = C.n + C.m;
+  const c64* Fe = F + e * aug_es + C.aug;
+  const c64* dr = Fe + (int64_t)r * ld;   // row r of D^{-1}
+  c64* xr = X + e * x_es + C.x + (int64_t)r * C.m;
+  const int32_t* cp = colptr + C.sp_cp;
+  for (int k = threadIdx.x; k < C.m; k += blockDim.x) {
+    c64 acc = make_double2(0.0, 0.0);
+    for (int t = cp[k]; t < cp[k + 1]; ++t) {
+      const int j = rows[t];
+      acc = cfma(acc, dr[j], Fe[(int64_t)j * ld + C.n + k]);
+    }
+    xr[k] = acc;
+  }
+}
+
+__global__ void k_leaf_schur(const LevelCluster* lc, const int32_t* colptr, const int32_t* rows,
+                             const c64* F, int64_t aug_es, const c64* X, int64_t x_es, c64* S,
+                             int64_t sq_es) {
+  const LevelCluster& C = lc[blockIdx.y];
+  const int k = blockIdx.x;
+  if (C.sp_cp < 0 || k >= C.m) return;
+  const int e = blockIdx.z;
+  const int64_t ld = C.n + C.m;
+  const c64* Fe = F + e * aug_es + C.aug;
+  const c64* Xe = X + e * x_es + C.x;
+  c64* sr = S + e * sq_es + C.sq + (int64_t)k * C.m;
+  const int32_t* cp = colptr + C.sp_cp;
+  const int t0 = cp[k], t1 = cp[k + 1];
+  for (int l = threadIdx.x; l < C.m; l += blockDim.x) {
+    c64 acc = sr[l];
+    for (int t = t0; t < t1; ++t) {
+      const int j = rows[t];
+      acc = cfms(acc, Fe[(int64_t)j * ld + C.n + k], Xe[(int64_t)j * C.m + l]);
+    }
+    sr[l] = acc;
+  }
+}
+
 // ---- a-posteriori check: diagonal residual of A G^r = I ---------------------------------------
 // Every non-zero A_uv joins two unknowns whose G^r entry lies in a stored block (same cluster, or
 // one in the other's update set; G^r = (G^r)^T for the complex-symmetric A of Eq. 1), so
@@ -738,6 +788,22 @@ cudaError_t launch_gj_move(const GJProb* probs, int nmat, int max_n, c64* F, int
   if (k0 >= max_n) return cudaSuccess;
   const int64_t tot = (int64_t)max_n * std::min(nb, max_n - k0);
   k_gj_move<<<dim3(blocks_for(tot, 256), nmat, ne), 256, 0, s>>>(probs, F, f_es, Mt, Rt, t_es, k0, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_x(const LevelCluster* lc, int nl, int max_n, const int32_t* colptr,
+                          const int32_t* rows, const c64* F, int64_t aug_es, c64* X, int64_t x_es, int ne,
+                          cudaStream_t s) {
+  if (nl <= 0 || max_n <= 0 || ne <= 0) return cudaSuccess;
+  k_leaf_x<<<dim3(max_n, nl, ne), 128, 0, s>>>(lc, colptr, rows, F, aug_es, X, x_es);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_schur(const LevelCluster* lc, int nl, int max_m, const int32_t* colptr,
+                              const int32_t* rows, const c64* F, int64_t aug_es, const c64* X, int64_t x_es,
+                              c64* S, int64_t sq_es, int ne, cudaStream_t s) {
+  if (nl <= 0 || max_m <= 0 || ne <= 0) return cudaSuccess;
+  k_leaf_schur<<<dim3(max_m, nl, ne), 128, 0, s>>>(lc, colptr, rows, F, aug_es, X, x_es, S, sq_es);
   return cudaGetLastError();
 }
 

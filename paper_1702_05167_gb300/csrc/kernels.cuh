@@ -19,6 +19,12 @@ cudaError_t launch_gj_panel(const GJProb* probs, int nmat, c64* F, int64_t f_es,
 cudaError_t launch_gj_swap(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,
                            const int32_t* piv, int64_t piv_es, c64* Rt, int64_t t_es, int k0, int nb,
                            int ne, cudaStream_t s, int c_lo = 0, int c_hi = 1 << 30);
+cudaError_t launch_leaf_x(const LevelCluster* lc, int nl, int max_n, const int32_t* colptr,
+                          const int32_t* rows, const c64* F, int64_t aug_es, c64* X, int64_t x_es, int ne,
+                          cudaStream_t s);
+cudaError_t launch_leaf_schur(const LevelCluster* lc, int nl, int max_m, const int32_t* colptr,
+                              const int32_t* rows, const c64* F, int64_t aug_es, const c64* X, int64_t x_es,
+                              c64* S, int64_t sq_es, int ne, cudaStream_t s);
 cudaError_t launch_gj_move(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es, c64* Mt,
                            c64* Rt, int64_t t_es, int k0, int nb, int ne, cudaStream_t s);
 cudaError_t launch_gj_colperm(const GJProb* probs, int nmat, int max_n, c64* F, int64_t f_es,

@@ -56,6 +56,7 @@ struct UpLevel {
   int64_t gji = 0;               // index into the nested-panel GJProb array
   int dense0 = 0, dense_n = 0;   // DENSE contact blocks of this level's clusters (dense_dev range)
   int64_t dense_max = 0;         // largest nu^2 among them
+  int sp_count = 0, sp_max_m = 0;   // leaves whose X and Schur products use the sparse A_iU
 };
 
 struct DownLevel {
@@ -68,12 +69,12 @@ struct DownLevel {
 };
 
 enum KClass { K_GEMM = 0, K_GEMM_TC, K_SCHUR, K_SCHUR_TC, K_GJ_PANEL, K_GJ_SWAP, K_GJ_PERM, K_ASSEMBLE, K_ADD_A, K_FOLD, K_GATHER,
-              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_RESID, K_GJU, K_GJU_TC, K_GJU_OZ, K_NCLASS };
+              K_OUT, K_GEMM_OZ, K_SCHUR_OZ, K_RESID, K_GJU, K_GJU_TC, K_GJU_OZ, K_LEAF, K_NCLASS };
 static const char* kClassName[K_NCLASS] = {"gemm_z_dmma", "gemm_tc_tf32x3", "schur_z_dmma",
                                            "schur_tc_tf32x3", "gj_panel", "gj_swap", "gj_colperm",
                                            "assemble", "add_a", "lesser_fold", "gather", "out",
                                            "gemm_z_ozaki", "schur_z_ozaki", "residual",
-                                           "gj_update_dmma", "gj_update_tc", "gj_update_ozaki"};
+                                           "gj_update_dmma", "gj_update_tc", "gj_update_ozaki", "leaf_sparse"};
 
 struct Prof {
   bool on = false;
@@ -139,6 +140,7 @@ struct DeviceState {
   void* io = nullptr;
   int64_t* poff = nullptr;
   int64_t pair_cap = 0;
+  int32_t *sp_colptr = nullptr, *sp_rows = nullptr;   // sparse A_iU of leaves (CSC, per cluster)
   DenseBlock* dense_dev = nullptr;   // DENSE contact blocks, grouped by upward level
   int32_t* dense_loc = nullptr;      // their slot -> local row maps
   const c64* dense_r = nullptr;      // set by hsc_solve_dense for one call: per-energy blocks,
@@ -349,10 +351,15 @@ int build_schedule(hsc_ctx* h) {
     L.map0 = P.map_off[2 * i] < 0 ? 0 : P.map_off[2 * i];
     L.map1 = P.map_off[2 * i + 1] < 0 ? 0 : P.map_off[2 * i + 1];
     L.h0 = P.h_off[i]; L.h1 = P.h_off[i + 1];
+    L.sp_cp = -1;
     L.own0 = P.own_off[i];
     L.u0 = P.u_off[i]; L.pm0 = P.pm_off[i]; L.nseg = P.nseg[i]; L.depth = c.depth;
     return L;
   };
+
+  // leaves whose X = D^{-1} A_iU and Schur update use A_iU's sparsity (the H couplings only)
+  std::vector<int32_t> spc, spr;
+  const bool leaf_sparse = h->opt_leaf_sparse != 0;
 
   // upward levels
   d->up.assign(P.by_height.size(), UpLevel());
@@ -364,6 +371,25 @@ int build_schedule(hsc_ctx* h) {
     int64_t el = 0, tt = 0, tz = 0, gjt = 0;
     for (int i : ids) {
       LevelCluster L = base_lc(i);
+      if (leaf_sparse && P.cl[i].nchild == 0 && L.m > 0) {
+        // a leaf's front holds no children's Schur complements: A_iU is the H entries (r, q >= n)
+        std::vector<std::vector<int32_t>> colr(L.m);
+        for (int64_t t = L.h0; t < L.h1; ++t) {
+          const int32_t r = P.h_rq[2 * t], q = P.h_rq[2 * t + 1];
+          if (q >= L.n) colr[q - L.n].push_back(r);
+        }
+        L.sp_cp = (int64_t)spc.size();
+        for (int k = 0; k < L.m; ++k) {
+          auto& v = colr[k];
+          std::sort(v.begin(), v.end());
+          v.erase(std::unique(v.begin(), v.end()), v.end());
+          spc.push_back((int32_t)spr.size());
+          spr.insert(spr.end(), v.begin(), v.end());
+        }
+        spc.push_back((int32_t)spr.size());
+        U.sp_count++;
+        U.sp_max_m = std::max(U.sp_max_m, L.m);
+      }
       L.elem_start = el;
       L.tt = tt; L.tz = tz; L.tn = 0;
       el += (int64_t)L.n * (L.n + L.m) + (int64_t)L.m * L.m;
@@ -406,12 +432,14 @@ int build_schedule(hsc_ctx* h) {
       GemmList g1(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
+        if (L.sp_cp >= 0) continue;   // sparse A_iU: k_leaf_x
         g1.add(L.n, L.m, L.n, L.aug, L.n + L.m, L.aug + L.n, L.n + L.m, L.x, L.m);
       }
       U.u1 = g1.args(OP_N, OP_N, 1, 0, 0, 0);
       GemmList g2(gps, gps128, gpsoz);
       for (int k = 0; k < U.nl; ++k) {
         const auto& L = lv[k];
+        if (L.sp_cp >= 0) continue;   // sparse A_iU: k_leaf_schur
         g2.add(L.m, L.m, L.n, L.aug + L.n, L.n + L.m, L.x, L.m, L.sq, L.m, L.sq, L.m, 1);
       }
       U.u2 = g2.args(OP_T, OP_N, -1, 0, 1, 0);
@@ -740,6 +768,10 @@ int build_schedule(hsc_ctx* h) {
   UP(&d->res_rowptr, h->rowptr);
   UP(&d->res_loc, rloc);
   UP(&d->unk_slot, uslot);
+  if (spc.empty()) spc.push_back(0);
+  if (spr.empty()) spr.push_back(0);
+  UP(&d->sp_colptr, spc);
+  UP(&d->sp_rows, spr);
   {
     // DENSE contact blocks grouped by the upward level of their cluster
     std::vector<DenseBlock> db;
@@ -964,9 +996,16 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
            launch_gj_colperm(gp, U.nmat, U.max_n, d->F, d->aug_es, d->piv, d->piv_es, ne, s,
                              d->growth_wave, d->cond_wave ? d->cond_wave + U.gj : nullptr, d->ncl));
     GEMM(U.u1, d->F, d->aug_es, d->F, d->aug_es, d->X, d->x_es, nullptr, 0);
+    if (U.sp_count > 0)
+      LAUNCH(K_LEAF, 1, 0.0, 0.0,
+             launch_leaf_x(lc, U.nl, U.max_n, d->sp_colptr, d->sp_rows, d->F, d->aug_es, d->X, d->x_es, ne, s));
     schur = true;
     GEMM(U.u2, d->F, d->aug_es, d->X, d->x_es, d->S, d->sq_es, d->S, d->sq_es);
     schur = false;
+    if (U.sp_count > 0)
+      LAUNCH(K_LEAF, 1, 0.0, 0.0,
+             launch_leaf_schur(lc, U.nl, U.sp_max_m, d->sp_colptr, d->sp_rows, d->F, d->aug_es, d->X, d->x_es,
+                               d->S, d->sq_es, ne, s));
     if (les && U.any_lesser) {
       GEMM(U.u3, d->L, d->aug_es, d->X, d->x_es, d->T, d->tt_es, d->L, d->aug_es);
       GEMM(U.u4, d->X, d->x_es, d->T, d->tt_es, d->Z, d->tz_es, nullptr, 0);

@@ -28,7 +28,7 @@ EXPORTS = ["hsc_create", "hsc_analyze", "hsc_cluster", "hsc_solve", "hsc_solve_b
            "hsc_mlp_forward", "hsc_mlp_loss_grad", "hsc_mlp_adam", "hsc_mlp_destroy"]
 HSC_OPT_GJ_PANEL, HSC_OPT_FP64_LEVELS, HSC_OPT_MIXED_GJ_FP64, HSC_OPT_LEAF, HSC_OPT_COMPLEX_4M = 1, 2, 3, 4, 5
 HSC_OPT_FP64_ENGINE, HSC_OPT_RESOLVE_DIGITS, HSC_OPT_TREE_VARIANT, HSC_OPT_ORDERING = 6, 7, 8, 9
-HSC_OPT_MAX_CLUSTER, HSC_OPT_TREE_FORM, HSC_OPT_GJ_WIDE, HSC_OPT_LEAF_BAND = 10, 11, 12, 13
+HSC_OPT_MAX_CLUSTER, HSC_OPT_TREE_FORM, HSC_OPT_GJ_WIDE, HSC_OPT_LEAF_BAND, HSC_OPT_LEAF_SPARSE = 10, 11, 12, 13, 14
 
 
 class hsc_tree_stats(ctypes.Structure):

@@ -302,10 +302,14 @@ def test_options_round_trip_and_reject_bad_values():
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF_BAND) == 1
     hsc.hsc_set_option(h, hsc.HSC_OPT_LEAF_BAND, 0)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF_BAND) == 0
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF_SPARSE) == 1
+    hsc.hsc_set_option(h, hsc.HSC_OPT_LEAF_SPARSE, 0)
+    assert hsc.hsc_get_option(h, hsc.HSC_OPT_LEAF_SPARSE) == 0
     for opt, val in ((hsc.HSC_OPT_GJ_PANEL, 0), (hsc.HSC_OPT_GJ_PANEL, 65), (99, 1),
                      (hsc.HSC_OPT_FP64_ENGINE, 3), (hsc.HSC_OPT_RESOLVE_DIGITS, 16),
                      (hsc.HSC_OPT_TREE_VARIANT, 5), (hsc.HSC_OPT_GJ_WIDE, -1), (hsc.HSC_OPT_GJ_WIDE, 513),
-                     (hsc.HSC_OPT_TREE_FORM, 1), (hsc.HSC_OPT_LEAF_BAND, 2), (hsc.HSC_OPT_LEAF_BAND, -1)):
+                     (hsc.HSC_OPT_TREE_FORM, 1), (hsc.HSC_OPT_LEAF_BAND, 2), (hsc.HSC_OPT_LEAF_BAND, -1),
+                     (hsc.HSC_OPT_LEAF_SPARSE, 2)):
         with pytest.raises(hsc.HSCError) as ei:
             hsc.hsc_set_option(h, opt, val)
         assert ei.value.code == hsc.HSC_ERR_ARG

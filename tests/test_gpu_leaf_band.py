@@ -1,9 +1,11 @@
-"""Leaf column bands (HSC_OPT_LEAF_BAND): the downward products of a leaf cluster form its G_ii and
+"""Leaf clusters. Column bands (HSC_OPT_LEAF_BAND): the downward products of a leaf cluster form its G_ii and
 G^<_ii blocks only on the column band, per block of <= 128 rows, that spans the entries read
 afterwards (diagonal, the residual check's H neighbours, requested pairs inside the block, and every
 column of a lesser leaf's contact rows). On the FP64-emulation engine each computed entry is the
 same exact digit sum rounded once, so the outputs must equal those of whole blocks bit for bit;
-both against the dense definition (Eqs. 1-2) at eta = 0.05."""
+both against the dense definition (Eqs. 1-2) at eta = 0.05. Sparse coupling blocks
+(HSC_OPT_LEAF_SPARSE): a leaf's X = D^{-1} A_iU and Schur update from the H pattern of A_iU, in FP64,
+against the dense block products and the dense definition."""
 import numpy as np
 import pytest
 
@@ -36,10 +38,11 @@ def _leaf_pairs(dev, s, count, seed):
     return np.array(out, dtype=np.int32)
 
 
-def _solve(dev, leaf, band, pairs, E, sr, sl, engine=2):
+def _solve(dev, leaf, band, pairs, E, sr, sl, engine=2, sparse=1):
     s = hsc.Solver(dev, leaf)
     hsc.hsc_set_option(s.h, hsc.HSC_OPT_FP64_ENGINE, engine)
     hsc.hsc_set_option(s.h, hsc.HSC_OPT_LEAF_BAND, band)
+    hsc.hsc_set_option(s.h, hsc.HSC_OPT_LEAF_SPARSE, sparse)
     out = s.solve(E, 0.05, sr, sl, pairs=pairs)
     res = hsc.hsc_residual(s.h, len(E))
     return s, out, res
@@ -125,3 +128,29 @@ def test_leaf_bands_with_dense_contact_blocks():
         outs.append(o)
     for x, y in zip(*outs):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("dims,leaf", [((15, 16, 16), 8), ((9, 7, 8), 3), ((12, 10, 9), 4)])
+def test_sparse_leaf_couplings_against_dense_products(dims, leaf):
+    """X and the Schur update of every leaf from A_iU's H pattern (FP64 gathers) against the dense
+    block products of the same tree: diag G^r, diag G^<, coupling and in-leaf pairs within 1e-12
+    of each other, both within 1e-10 of the dense definition; residuals within 1e-12 absolute."""
+    dev = W.cubic_device(dims, W=1.0, seed=12)
+    E = np.array([-2.1, 0.6])
+    sr, sl = W.self_energies(dev, len(E))
+    s0 = hsc.Solver(dev, leaf)
+    pairs = np.concatenate([W.plane_pairs(dev, dims[0] // 2), _leaf_pairs(dev, s0, 30, 4)])
+    s0.close()
+    ss, osp, rsp = _solve(dev, leaf, 1, pairs, E, sr, sl, engine=0, sparse=1)
+    sd, odn, rdn = _solve(dev, leaf, 1, pairs, E, sr, sl, engine=0, sparse=0)
+    for a, b in zip(osp, odn):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert np.abs(rsp - rdn).max() <= 1e-12
+    Hd = dev.to_scipy().toarray()
+    for k in range(len(E)):
+        G, Gl = dense.solve(Hd, E[k], 0.05, dev.contact_unknowns(), sr[k], sl[k])
+        for x, ref in ((osp[0][k], np.diag(G)), (osp[1][k], np.diag(Gl)),
+                       (osp[2][k], G[pairs[:, 0], pairs[:, 1]]), (osp[3][k], Gl[pairs[:, 0], pairs[:, 1]])):
+            assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+    ss.close()
+    sd.close()
