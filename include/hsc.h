@@ -244,7 +244,11 @@ typedef enum {
                               /* complements, so its coupling block A_iU is the H entries alone:*/
                               /* X = D^{-1} A_iU and the Schur update A_iU^T X are formed as     */
                               /* gathers over that pattern in FP64 (the dense products' other   */
-                              /* terms are exact zeros). 0: dense block products                */
+                              /* terms are exact zeros); and its diagonal block is banded in the */
+                              /* local order (bandwidth b, no DENSE contact block on it), so the */
+                              /* nested Gauss-Jordan steps skip the rows at positions >= k + b   */
+                              /* (untouched until pivot k) and the columns beyond the pivot     */
+                              /* rows' reach k + 2b. 0: dense block products and inversion      */
   HSC_OPT_TREE_FORM = 11      /* read only: the tree of the last hsc_analyze: 0 plain geometric,*/
                               /* 1 contact-connected geometric, 2 graph bisection (-1 before    */
                               /* any analysis). With HSC_OPT_ORDERING = 0 the contact-connected */

@@ -77,6 +77,10 @@ cudaError_t gemm_oz(const GemmArgs& g, int n_energy, uint16_t* slices, int64_t s
 struct GJProb {
   int n, ld;
   int64_t off, piv_off, mt_off, rt_off;
+  int band;   // > 0: the block is banded, |r - c| <= band where non-zero (a leaf's stencil in its local
+              // order); Gauss-Jordan with partial pivoting then leaves the rows at positions >= k + band
+              // untouched until pivot k, and pivot row j has no non-zero beyond column j + 2 band.
+              // 0: dense
 };
 
 // Per-level description of the clusters for the element-wise kernels.

@@ -130,6 +130,8 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
   if (k0 >= n) return;
   const int w = min(nb, n - k0);
+  // banded block: rows at positions >= k0 + w + band are untouched and zero in the panel's columns
+  const int nr = P.band > 0 ? min(n, k0 + w + P.band) : n;
   c64* A = F + e * f_es + P.off;
   int32_t* pv = piv + e * piv_es + P.piv_off;
   __shared__ double s_v[GJ_THREADS / 32];
@@ -140,7 +142,7 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   for (int j = k0; j < k0 + w; ++j) {
     double best = -1.0;
     int bi = n;
-    for (int r = j + tid; r < n; r += GJ_THREADS) {
+    for (int r = j + tid; r < nr; r += GJ_THREADS) {
       c64 v = A[(int64_t)r * ld + j];
       double a = fabs(v.x) + fabs(v.y);
       if (a > best) { best = a; bi = r; }
@@ -179,7 +181,7 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
       s_pr[c] = nv;
     }
     __syncthreads();
-    for (int r = tid; r < n; r += GJ_THREADS) {
+    for (int r = tid; r < nr; r += GJ_THREADS) {
       if (r == j) continue;
       c64* row = A + (int64_t)r * ld;
       const c64 f = row[j];
@@ -193,7 +195,7 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   }
   c64* M = Mt + e * t_es + P.mt_off;
   c64* R = Rt + e * t_es + P.rt_off;
-  for (int idx = tid; idx < n * w; idx += GJ_THREADS) {
+  for (int idx = tid; idx < nr * w; idx += GJ_THREADS) {   // M's rows >= nr are not read
     int r = idx / w, c = idx % w;
     M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
     A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
@@ -226,6 +228,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
   const int e = blockIdx.y, n = P.n, ld = P.ld, tid = threadIdx.x;
   if (k0 >= n) return;   // uniform over the cluster
   const int w = min(nb, n - k0);
+  const int nr = P.band > 0 ? min(n, k0 + w + P.band) : n;   // as in k_gj_panel
   c64* A = F + e * f_es + P.off;
   int32_t* pv = piv + e * piv_es + P.piv_off;
   __shared__ double s_v[GJ_THREADS / 32];
@@ -240,7 +243,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
   for (int j = k0; j < k0 + w; ++j) {
     double best = -1.0;
     int bi = n;
-    for (int r = r_first; r < n; r += r_step) {
+    for (int r = r_first; r < nr; r += r_step) {
       if (r < j) continue;
       c64 v = A[(int64_t)r * ld + j];
       double a = fabs(v.x) + fabs(v.y);
@@ -294,7 +297,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
     if (p != j && owner(p) == q)
       for (int c = tid; c < w; c += GJ_THREADS) A[(int64_t)p * ld + k0 + c] = s_old[c];
     __syncthreads();
-    for (int r = r_first; r < n; r += r_step) {
+    for (int r = r_first; r < nr; r += r_step) {
       if (r == j) continue;
       c64* row = A + (int64_t)r * ld;
       const c64 f = row[j];
@@ -308,7 +311,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
   }
   c64* M = Mt + e * t_es + P.mt_off;
   c64* R = Rt + e * t_es + P.rt_off;
-  for (int r = r_first; r < n; r += r_step)
+  for (int r = r_first; r < nr; r += r_step)
     for (int c = 0; c < w; ++c) {
       M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
       A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
@@ -333,6 +336,11 @@ __global__ void k_gj_swap(const GJProb* probs, c64* F, int64_t f_es, const int32
   if (c >= k0 && c < k0 + w) return;
   c64* A = F + e * f_es + P.off;
   const int32_t* pv = piv + e * piv_es + P.piv_off;
+  if (P.band > 0 && c >= k0 + w + 2 * P.band) {   // banded: the pivot rows are zero in this column
+    c64* R = Rt + e * t_es + P.rt_off;
+    for (int t = 0; t < w; ++t) R[(int64_t)t * n + c] = make_double2(0.0, 0.0);
+    return;
+  }
   for (int j = k0; j < k0 + w; ++j) {
     int p = pv[j];
     if (p != j) {

@@ -360,6 +360,7 @@ int build_schedule(hsc_ctx* h) {
   // leaves whose X = D^{-1} A_iU and Schur update use A_iU's sparsity (the H couplings only)
   std::vector<int32_t> spc, spr;
   const bool leaf_sparse = h->opt_leaf_sparse != 0;
+  const bool leaf_band_gj = h->opt_leaf_sparse != 0;   // banded Gauss-Jordan of the leaves' blocks
 
   // upward levels
   d->up.assign(P.by_height.size(), UpLevel());
@@ -409,6 +410,18 @@ int build_schedule(hsc_ctx* h) {
       d->gj_owner.push_back(i);
       GJProb g{};
       g.n = L.n; g.ld = L.n + L.m; g.off = L.aug; g.piv_off = L.own0;
+      // a leaf's diagonal block is the H pattern (plus the diagonal) unless a DENSE contact block is
+      // added to it: its bandwidth in the local order bounds the Gauss-Jordan steps (nested path)
+      if (nbo && leaf_band_gj && P.cl[i].nchild == 0) {
+        bool dense_here = false;
+        for (const auto& Dn : P.dense) dense_here |= Dn.cluster == i;
+        int64_t b = 0;
+        for (int64_t t = L.h0; t < L.h1; ++t) {
+          const int32_t r = P.h_rq[2 * t], q = P.h_rq[2 * t + 1];
+          if (q < L.n) b = std::max<int64_t>(b, r > q ? r - q : q - r);
+        }
+        if (!dense_here && b > 0 && 2 * b < L.n) g.band = (int)b;
+      }
       const int wo = nbo ? nbo : nb;   // M: n x wo, R: wo x n
       g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * wo;
       gjt += 2 * (int64_t)L.n * wo;
@@ -489,7 +502,9 @@ int build_schedule(hsc_ctx* h) {
               const GJProb& q = gi[k];
               if (q.n <= k0) continue;
               const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
-              gs.add(q.n, wo, w, q.mt_off, nb, q.rt_off + k1, q.n, q.off + k1, q.ld, q.off + k1, q.ld, 1,
+              // banded leaf: rows >= k0 + w + band are untouched by the panel's pivots
+              const int mr = q.band > 0 ? std::min(q.n, k0 + w + q.band) : q.n;
+              gs.add(mr, wo, w, q.mt_off, nb, q.rt_off + k1, q.n, q.off + k1, q.ld, q.off + k1, q.ld, 1,
                      k0, k0 + w);
             }
             U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
@@ -501,7 +516,10 @@ int build_schedule(hsc_ctx* h) {
             const GJProb& q = gl[k];
             if (q.n <= k1) continue;
             const int wo = std::min(nbo, q.n - k1);
-            gs.add(q.n, q.n, wo, q.mt_off, nbo, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k1, k1 + wo);
+            // banded leaf: rows >= k1 + wo + band untouched, pivot rows zero from column k1 + wo + 2 band
+            const int mr = q.band > 0 ? std::min(q.n, k1 + wo + q.band) : q.n;
+            const int nc = q.band > 0 ? std::min(q.n, k1 + wo + 2 * q.band) : q.n;
+            gs.add(mr, nc, wo, q.mt_off, nbo, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k1, k1 + wo);
           }
           U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
           U.sdesc.push_back(GjStep{2, k1, k1});
