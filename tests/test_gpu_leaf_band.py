@@ -154,3 +154,26 @@ def test_sparse_leaf_couplings_against_dense_products(dims, leaf):
             assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
     ss.close()
     sd.close()
+
+
+def test_banded_inversion_with_pivots_below_the_diagonal():
+    """Weak disorder at E ~ 0: the leaves' diagonal entries (E - eps_i, |eps_i| <= 0.1) are small
+    against the hopping, so partial pivoting takes most pivots from rows below the diagonal, up to
+    the bandwidth. The banded Gauss-Jordan (HSC_OPT_LEAF_SPARSE = 1) must still give the dense
+    definition at 1e-10 and the dense-block path within 1e-12."""
+    dims = (14, 9, 9)
+    dev = W.cubic_device(dims, W=0.2, seed=21)
+    E = np.array([0.0, 0.05, -0.03])
+    sr, sl = W.self_energies(dev, len(E))
+    pairs = W.plane_pairs(dev, dims[0] // 2)
+    ss, osp, _ = _solve(dev, 4, 1, pairs, E, sr, sl, engine=0, sparse=1)
+    sd, odn, _ = _solve(dev, 4, 1, pairs, E, sr, sl, engine=0, sparse=0)
+    for a, b in zip(osp, odn):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    Hd = dev.to_scipy().toarray()
+    for k in range(len(E)):
+        G, Gl = dense.solve(Hd, E[k], 0.05, dev.contact_unknowns(), sr[k], sl[k])
+        for x, ref in ((osp[0][k], np.diag(G)), (osp[1][k], np.diag(Gl)), (osp[2][k], G[pairs[:, 0], pairs[:, 1]])):
+            assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+    ss.close()
+    sd.close()
