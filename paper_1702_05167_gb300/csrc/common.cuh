@@ -81,6 +81,12 @@ struct GJProb {
               // order); Gauss-Jordan with partial pivoting then leaves the rows at positions >= k + band
               // untouched until pivot k, and pivot row j has no non-zero beyond column j + 2 band.
               // 0: dense
+  int wide;   // > 0: nested blocking with wide panels of this width whose rows above the wide panel
+              // are deferred: the panels and their products touch rows >= k1 (the wide panel's
+              // start) only and carry `wide` virtual rows (identity at k1, at offset tv_off, ld wide;
+              // their panel columns go to mv_off) that become the wide panel's transform T; the
+              // trailing product applies T R (at bp_off, ld n) to the rows above
+  int64_t tv_off, mv_off, bp_off;
 };
 
 // Per-level description of the clusters for the element-wise kernels.

@@ -52,6 +52,8 @@ struct UpLevel {
   int64_t gj = 0;           // index into the GJProb array
   int nmat = 0;
   std::vector<GemmPair> steps;
+  std::vector<GemmPair> vsteps;  // per step, the products on the Gauss-Jordan scratch (deferred rows):
+                                 // the virtual rows' update (nested steps), T R (wide-panel steps)
   std::vector<GjStep> sdesc;     // what each entry of steps is
   int64_t gji = 0;               // index into the nested-panel GJProb array
   int dense0 = 0, dense_n = 0;   // DENSE contact blocks of this level's clusters (dense_dev range)
@@ -425,6 +427,13 @@ int build_schedule(hsc_ctx* h) {
       const int wo = nbo ? nbo : nb;   // M: n x wo, R: wo x n
       g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * wo;
       gjt += 2 * (int64_t)L.n * wo;
+      if (nbo && L.n > nbo) {   // deferred rows above each wide panel: T (wo x wo), its panel columns
+                                // (wo x nb) and T R (wo x n) on the scratch
+        g.wide = nbo;
+        g.tv_off = gjt; gjt += (int64_t)nbo * nbo;
+        g.mv_off = gjt; gjt += (int64_t)nbo * nb;
+        g.bp_off = gjt; gjt += (int64_t)nbo * L.n;
+      }
       gjs.push_back(g);
       if (nbo) {   // the nested panels' M (n x nb) and R (nb x n)
         GJProb gi = g;
@@ -490,6 +499,7 @@ int build_schedule(hsc_ctx* h) {
             gs.add(q.n, q.n, w, q.mt_off, nb, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k0, k0 + w);
           }
           U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+          U.vsteps.push_back(GemmList(gps, gps128, gpsoz).args(OP_N, OP_N, 1, 0, 1, 0));
           U.sdesc.push_back(GjStep{0, k0, 0});
         }
       } else {
@@ -504,24 +514,58 @@ int build_schedule(hsc_ctx* h) {
               const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
               // banded leaf: rows >= k0 + w + band are untouched by the panel's pivots
               const int mr = q.band > 0 ? std::min(q.n, k0 + w + q.band) : q.n;
-              gs.add(mr, wo, w, q.mt_off, nb, q.rt_off + k1, q.n, q.off + k1, q.ld, q.off + k1, q.ld, 1,
-                     k0, k0 + w);
+              // deferred rows: rows >= k1 here, the rows above through the virtual rows' T
+              const int r0 = q.wide > 0 ? k1 : 0;
+              const int64_t ro = (int64_t)r0 * q.ld;
+              gs.add(mr - r0, wo, w, q.mt_off + (int64_t)r0 * nb, nb, q.rt_off + k1, q.n, q.off + ro + k1, q.ld,
+                     q.off + ro + k1, q.ld, 1, k0 - r0, k0 + w - r0);
             }
             U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+            GemmList gv(gps, gps128, gpsoz);   // the virtual rows (a list of its own: lists are contiguous)
+            for (int k = 0; k < U.nl; ++k) {
+              const GJProb& q = gi[k];
+              if (q.n <= k0 || q.wide <= 0 || k1 == 0) continue;
+              const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
+              gv.add(wo, wo, w, q.mv_off, nb, q.rt_off + k1, q.n, q.tv_off, q.wide, q.tv_off, q.wide, 1);
+            }
+            U.vsteps.push_back(gv.args(OP_N, OP_N, 1, 0, 1, 0));
             U.sdesc.push_back(GjStep{1, k0, k1});
           }
           // the wide panel's trailing product over the whole block, K = wo
+          // banded leaf: rows >= k1 + wo + band untouched, pivot rows zero from column k1 + wo + 2 band
+          auto bounds = [&](const GJProb& q, int wo, int& mr, int& nc) {
+            mr = q.band > 0 ? std::min(q.n, k1 + wo + q.band) : q.n;
+            nc = q.band > 0 ? std::min(q.n, k1 + wo + 2 * q.band) : q.n;
+          };
           GemmList gs(gps, gps128, gpsoz);
           for (int k = 0; k < U.nl; ++k) {
             const GJProb& q = gl[k];
             if (q.n <= k1) continue;
             const int wo = std::min(nbo, q.n - k1);
-            // banded leaf: rows >= k1 + wo + band untouched, pivot rows zero from column k1 + wo + 2 band
-            const int mr = q.band > 0 ? std::min(q.n, k1 + wo + q.band) : q.n;
-            const int nc = q.band > 0 ? std::min(q.n, k1 + wo + 2 * q.band) : q.n;
-            gs.add(mr, nc, wo, q.mt_off, nbo, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k1, k1 + wo);
+            int mr, nc;
+            bounds(q, wo, mr, nc);
+            if (q.wide > 0 && k1 > 0) {
+              // rows below k1 as before; the rows above, still untransformed in the wide panel's
+              // columns, take (their wide-panel part) x (T R), formed first on the scratch
+              const int64_t ro = (int64_t)k1 * q.ld;
+              gs.add(mr - k1, nc, wo, q.mt_off + (int64_t)k1 * nbo, nbo, q.rt_off, q.n, q.off + ro, q.ld,
+                     q.off + ro, q.ld, 1, 0, wo);
+              gs.add(k1, nc, wo, q.mt_off, nbo, q.bp_off, q.n, q.off, q.ld, q.off, q.ld, 1);
+            } else {
+              gs.add(mr, nc, wo, q.mt_off, nbo, q.rt_off, q.n, q.off, q.ld, q.off, q.ld, 1, k1, k1 + wo);
+            }
           }
           U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
+          GemmList gv(gps, gps128, gpsoz);   // T R
+          for (int k = 0; k < U.nl; ++k) {
+            const GJProb& q = gl[k];
+            if (q.n <= k1 || q.wide <= 0 || k1 == 0) continue;
+            const int wo = std::min(nbo, q.n - k1);
+            int mr, nc;
+            bounds(q, wo, mr, nc);
+            gv.add(wo, nc, wo, q.tv_off, q.wide, q.rt_off, q.n, q.bp_off, q.n);
+          }
+          U.vsteps.push_back(gv.args(OP_N, OP_N, 1, 0, 0, 0));
           U.sdesc.push_back(GjStep{2, k1, k1});
         }
       }
@@ -739,6 +783,7 @@ int build_schedule(hsc_ctx* h) {
     for (auto& U : d->up) {
       upd(U.u1); upd(U.u2); upd(U.u3); upd(U.u4);
       for (auto& st : U.steps) upd(st);
+      for (auto& st : U.vsteps) upd(st);
     }
     for (auto& D : d->down)
       for (auto& g : D.d) upd(g);
@@ -826,6 +871,7 @@ int build_schedule(hsc_ctx* h) {
   for (auto& U : d->up) {
     patch(U.u1); patch(U.u2); patch(U.u3); patch(U.u4);
     for (auto& s : U.steps) patch(s);
+    for (auto& s : U.vsteps) patch(s);
   }
   for (auto& D : d->down)
     for (auto& g : D.d) patch(g);
@@ -1006,7 +1052,11 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       const bool keep = tc;
       tc = tc && !d->gj_fp64;
       gjup = true;
+      if (sd.kind == 2)   // T R before the trailing product reads it
+        GEMM(U.vsteps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es, nullptr, 0);
       GEMM(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es);
+      if (sd.kind == 1)   // the virtual rows' update (the deferred rows' transform)
+        GEMM(U.vsteps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es);
       gjup = false;
       tc = keep;
     }
