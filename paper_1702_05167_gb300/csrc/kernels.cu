@@ -118,7 +118,7 @@ __global__ void k_add_diag(const LevelCluster* lc, const int32_t* own_contact, c
 
 // ---- Gauss-Jordan -----------------------------------------------------------------------------
 
-constexpr int GJ_THREADS = 256;
+constexpr int GJ_THREADS = 128;   // more resident panels per SM: a pivot step is latency-bound
 
 // Unblocked Gauss-Jordan on the panel columns [k0, k0+w) of every row, with the pivot of column j
 // chosen as the largest |re|+|im| among rows j..n-1 and the swap confined to the panel; then the
