@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 # and table are in profiles/launches_cubic32x64E_fp64.md). Valid only for the kernel source it was
 # taken on: bench.py reports null once csrc/gemm_oz.cu differs from that source.
 OZ_TRAFFIC = {"gemm_oz_sha256": "9e8ad2f7aa2a930208ae41ec3e5e3a8ce60bab6f9403a74b7da63270571758e7",
-              "bytes_per_class_launch": 3.815e9, "launches_per_solve": 576}
+              "bytes_per_class_launch": 2.406e9, "launches_per_solve": 918}
 sys.path.insert(0, ROOT)
 
 METRIC = "energy pts/s for diag(G^r,G^<) on 32^3 grid"
