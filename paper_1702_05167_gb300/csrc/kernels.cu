@@ -120,9 +120,12 @@ __global__ void k_add_diag(const LevelCluster* lc, const int32_t* own_contact, c
 
 constexpr int GJ_THREADS = 128;   // more resident panels per SM: a pivot step is latency-bound
 
-// Unblocked Gauss-Jordan on the panel columns [k0, k0+w) of every row, with the pivot of column j
-// chosen as the largest |re|+|im| among rows j..n-1 and the swap confined to the panel; then the
-// panel is moved to M (and zeroed in place) and the identity part of R is written.
+// Unblocked Gauss-Jordan on the panel columns [k0, k0+w), with the pivot of column j chosen as the
+// largest |re|+|im| among rows j..n-1 and the swap confined to the panel; then the panel is moved
+// to M (and zeroed in place) and the identity part of R is written. Rows taken: all of them, or
+// with a wide panel [k1, k1 + wide) (GJProb::wide) rows >= k1 plus the virtual rows that carry the
+// wide panel's transform for the rows above; on a banded block only rows < k0 + w + band (the
+// rest are untouched and zero in these columns).
 __global__ void __launch_bounds__(GJ_THREADS)
 k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_es, c64* Mt,
            c64* Rt, int64_t t_es, int k0, int nb, int* flag) {
