@@ -83,10 +83,9 @@ struct GJProb {
               // 0: dense
   int wide;   // > 0: nested blocking with wide panels of this width whose rows above the wide panel
               // are deferred: the panels and their products touch rows >= k1 (the wide panel's
-              // start) only and carry `wide` virtual rows (identity at k1, at offset tv_off, ld wide;
-              // their panel columns go to mv_off) that become the wide panel's transform T; the
-              // trailing product applies T R (at bp_off, ld n) to the rows above
-  int64_t tv_off, mv_off, bp_off;
+              // start) only; the trailing product applies T R (at bp_off, ld n) to the rows above,
+              // T = -P^{-1} the wide panel's transform of a non-pivot row (P its pivot block)
+  int64_t bp_off;
 };
 
 // Per-level description of the clusters for the element-wise kernels.

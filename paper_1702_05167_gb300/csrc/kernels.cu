@@ -123,9 +123,9 @@ constexpr int GJ_THREADS = 128;   // more resident panels per SM: a pivot step i
 // Unblocked Gauss-Jordan on the panel columns [k0, k0+w), with the pivot of column j chosen as the
 // largest |re|+|im| among rows j..n-1 and the swap confined to the panel; then the panel is moved
 // to M (and zeroed in place) and the identity part of R is written. Rows taken: all of them, or
-// with a wide panel [k1, k1 + wide) (GJProb::wide) rows >= k1 plus the virtual rows that carry the
-// wide panel's transform for the rows above; on a banded block only rows < k0 + w + band (the
-// rest are untouched and zero in these columns).
+// with a wide panel [k1, k1 + wide) (GJProb::wide) rows >= k1 (the rows above take the wide
+// panel's whole transform in its trailing product); on a banded block only rows < k0 + w + band
+// (the rest are untouched and zero in these columns).
 __global__ void __launch_bounds__(GJ_THREADS)
 k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_es, c64* Mt,
            c64* Rt, int64_t t_es, int k0, int nb, int* flag) {
@@ -135,11 +135,8 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   const int w = min(nb, n - k0);
   // banded block: rows at positions >= k0 + w + band are untouched and zero in the panel's columns
   const int nr = P.band > 0 ? min(n, k0 + w + P.band) : n;
-  // deferred rows: only rows >= k1 are eliminated here; nv virtual rows (no pivots among them)
-  // accumulate the wide panel's transform of the rows above
+  // deferred rows: only rows >= k1 (the wide panel's start) are eliminated here
   const int k1 = P.wide > 0 ? (k0 / P.wide) * P.wide : 0;
-  const int nv = (P.wide > 0 && k1 > 0) ? min(P.wide, n - k1) : 0;
-  c64* Tv = Mt + e * t_es + P.tv_off;
   c64* A = F + e * f_es + P.off;
   int32_t* pv = piv + e * piv_es + P.piv_off;
   __shared__ double s_v[GJ_THREADS / 32];
@@ -147,11 +144,6 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
   __shared__ int s_p;
   __shared__ c64 s_inv;
   __shared__ c64 s_pr[64];   // the scaled new row j (panel width <= 64)
-  if (nv > 0 && k0 == k1) {   // the wide panel starts: T = identity
-    for (int idx = tid; idx < nv * nv; idx += GJ_THREADS)
-      Tv[(int64_t)(idx / nv) * P.wide + idx % nv] = make_double2(idx / nv == idx % nv ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-  }
   for (int j = k0; j < k0 + w; ++j) {
     double best = -1.0;
     int bi = n;
@@ -194,11 +186,9 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
       s_pr[c] = nv;
     }
     __syncthreads();
-    // rows k1..nr-1 of the block, then the virtual rows (panel columns k0 - k1 + c of T)
-    for (int q = tid; q < nr - k1 + nv; q += GJ_THREADS) {
-      const int r = k1 + q;
-      if (q < nr - k1 && r == j) continue;
-      c64* row = q < nr - k1 ? A + (int64_t)r * ld + k0 : Tv + (int64_t)(q - (nr - k1)) * P.wide + (k0 - k1);
+    for (int r = k1 + tid; r < nr; r += GJ_THREADS) {
+      if (r == j) continue;
+      c64* row = A + (int64_t)r * ld + k0;
       const int jc = j - k0;
       const c64 f = row[jc];
       for (int c = 0; c < w; ++c) {
@@ -215,15 +205,6 @@ k_gj_panel(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t piv_
     int r = idx / w, c = idx % w;
     M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];
     A[(int64_t)r * ld + k0 + c] = make_double2(0.0, 0.0);
-  }
-  if (nv > 0) {
-    c64* Mv = Mt + e * t_es + P.mv_off;
-    for (int idx = tid; idx < nv * w; idx += GJ_THREADS) {
-      const int t = idx / w, c = idx % w;
-      c64* x = Tv + (int64_t)t * P.wide + (k0 - k1) + c;
-      Mv[(int64_t)t * nb + c] = *x;
-      *x = make_double2(0.0, 0.0);
-    }
   }
   for (int idx = tid; idx < w * w; idx += GJ_THREADS) {
     int t = idx / w, c = idx % w;
@@ -255,8 +236,6 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
   const int w = min(nb, n - k0);
   const int nr = P.band > 0 ? min(n, k0 + w + P.band) : n;   // as in k_gj_panel
   const int k1 = P.wide > 0 ? (k0 / P.wide) * P.wide : 0;    // deferred rows, as in k_gj_panel
-  const int nv = (P.wide > 0 && k1 > 0) ? min(P.wide, n - k1) : 0;
-  c64* Tv = Mt + e * t_es + P.tv_off;
   c64* A = F + e * f_es + P.off;
   int32_t* pv = piv + e * piv_es + P.piv_off;
   __shared__ double s_v[GJ_THREADS / 32];
@@ -268,11 +247,7 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
   __shared__ c64 s_pr[64], s_old[64];   // scaled new row j, old row j (panel width <= 64)
   auto owner = [&](int r) { return (r / GJ_THREADS) % CS; };
   const int r_first = q * GJ_THREADS + tid, r_step = CS * GJ_THREADS;
-  // virtual rows t with t % CS == q belong to CTA q (initialised and eliminated by it alone)
-  const int t_first = q + CS * tid, t_step = CS * GJ_THREADS;
-  if (nv > 0 && k0 == k1)
-    for (int t = t_first; t < nv; t += t_step)
-      for (int c = 0; c < nv; ++c) Tv[(int64_t)t * P.wide + c] = make_double2(t == c ? 1.0 : 0.0, 0.0);
+
   for (int j = k0; j < k0 + w; ++j) {
     double best = -1.0;
     int bi = n;
@@ -340,29 +315,11 @@ k_gj_panel_cl(const GJProb* probs, c64* F, int64_t f_es, int32_t* piv, int64_t p
       }
       row[j] = cneg(cmul(f, inv));
     }
-    for (int t = t_first; t < nv; t += t_step) {
-      c64* row = Tv + (int64_t)t * P.wide + (k0 - k1);
-      const int jc = j - k0;
-      const c64 f = row[jc];
-      for (int c = 0; c < w; ++c) {
-        if (c == jc) continue;
-        row[c] = cfms(row[c], f, s_pr[c]);
-      }
-      row[jc] = cneg(cmul(f, inv));
-    }
+
     __syncthreads();   // this CTA's rows are complete before its next candidate search
   }
   c64* M = Mt + e * t_es + P.mt_off;
   c64* R = Rt + e * t_es + P.rt_off;
-  if (nv > 0) {
-    c64* Mv = Mt + e * t_es + P.mv_off;
-    for (int t = t_first; t < nv; t += t_step)
-      for (int c = 0; c < w; ++c) {
-        c64* x = Tv + (int64_t)t * P.wide + (k0 - k1) + c;
-        Mv[(int64_t)t * nb + c] = *x;
-        *x = make_double2(0.0, 0.0);
-      }
-  }
   for (int r = r_first; r < nr; r += r_step)
     for (int c = 0; c < w && r >= k1; ++c) {
       M[(int64_t)r * nb + c] = A[(int64_t)r * ld + k0 + c];

@@ -52,8 +52,8 @@ struct UpLevel {
   int64_t gj = 0;           // index into the GJProb array
   int nmat = 0;
   std::vector<GemmPair> steps;
-  std::vector<GemmPair> vsteps;  // per step, the products on the Gauss-Jordan scratch (deferred rows):
-                                 // the virtual rows' update (nested steps), T R (wide-panel steps)
+  std::vector<GemmPair> vsteps;  // per step, a product on the Gauss-Jordan scratch (deferred rows):
+                                 // T R before a wide panel's trailing product, else empty
   std::vector<GjStep> sdesc;     // what each entry of steps is
   int64_t gji = 0;               // index into the nested-panel GJProb array
   int dense0 = 0, dense_n = 0;   // DENSE contact blocks of this level's clusters (dense_dev range)
@@ -427,11 +427,8 @@ int build_schedule(hsc_ctx* h) {
       const int wo = nbo ? nbo : nb;   // M: n x wo, R: wo x n
       g.mt_off = gjt; g.rt_off = gjt + (int64_t)L.n * wo;
       gjt += 2 * (int64_t)L.n * wo;
-      if (nbo && L.n > nbo) {   // deferred rows above each wide panel: T (wo x wo), its panel columns
-                                // (wo x nb) and T R (wo x n) on the scratch
+      if (nbo && L.n > nbo) {   // deferred rows above each wide panel: T R (wo x n) on the scratch
         g.wide = nbo;
-        g.tv_off = gjt; gjt += (int64_t)nbo * nbo;
-        g.mv_off = gjt; gjt += (int64_t)nbo * nb;
         g.bp_off = gjt; gjt += (int64_t)nbo * L.n;
       }
       gjs.push_back(g);
@@ -514,21 +511,14 @@ int build_schedule(hsc_ctx* h) {
               const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
               // banded leaf: rows >= k0 + w + band are untouched by the panel's pivots
               const int mr = q.band > 0 ? std::min(q.n, k0 + w + q.band) : q.n;
-              // deferred rows: rows >= k1 here, the rows above through the virtual rows' T
+              // deferred rows: rows >= k1 here, the rows above in the wide panel's trailing product
               const int r0 = q.wide > 0 ? k1 : 0;
               const int64_t ro = (int64_t)r0 * q.ld;
               gs.add(mr - r0, wo, w, q.mt_off + (int64_t)r0 * nb, nb, q.rt_off + k1, q.n, q.off + ro + k1, q.ld,
                      q.off + ro + k1, q.ld, 1, k0 - r0, k0 + w - r0);
             }
             U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
-            GemmList gv(gps, gps128, gpsoz);   // the virtual rows (a list of its own: lists are contiguous)
-            for (int k = 0; k < U.nl; ++k) {
-              const GJProb& q = gi[k];
-              if (q.n <= k0 || q.wide <= 0 || k1 == 0) continue;
-              const int w = std::min(nb, q.n - k0), wo = std::min(nbo, q.n - k1);
-              gv.add(wo, wo, w, q.mv_off, nb, q.rt_off + k1, q.n, q.tv_off, q.wide, q.tv_off, q.wide, 1);
-            }
-            U.vsteps.push_back(gv.args(OP_N, OP_N, 1, 0, 1, 0));
+            U.vsteps.push_back(GemmList(gps, gps128, gpsoz).args(OP_N, OP_N, 1, 0, 1, 0));
             U.sdesc.push_back(GjStep{1, k0, k1});
           }
           // the wide panel's trailing product over the whole block, K = wo
@@ -546,7 +536,9 @@ int build_schedule(hsc_ctx* h) {
             bounds(q, wo, mr, nc);
             if (q.wide > 0 && k1 > 0) {
               // rows below k1 as before; the rows above, still untransformed in the wide panel's
-              // columns, take (their wide-panel part) x (T R), formed first on the scratch
+              // columns, take (their wide-panel part) x (T R), formed first on the scratch: the wide
+              // panel's transform of a non-pivot row is T = -P^{-1}, P its pivot block, and its pivot
+              // rows hold P^{-1} in the wide panel's columns (moved to M rows k1..k1 + wo)
               const int64_t ro = (int64_t)k1 * q.ld;
               gs.add(mr - k1, nc, wo, q.mt_off + (int64_t)k1 * nbo, nbo, q.rt_off, q.n, q.off + ro, q.ld,
                      q.off + ro, q.ld, 1, 0, wo);
@@ -556,16 +548,16 @@ int build_schedule(hsc_ctx* h) {
             }
           }
           U.steps.push_back(gs.args(OP_N, OP_N, 1, 0, 1, 0));
-          GemmList gv(gps, gps128, gpsoz);   // T R
+          GemmList gv(gps, gps128, gpsoz);   // T R = -P^{-1} R
           for (int k = 0; k < U.nl; ++k) {
             const GJProb& q = gl[k];
             if (q.n <= k1 || q.wide <= 0 || k1 == 0) continue;
             const int wo = std::min(nbo, q.n - k1);
             int mr, nc;
             bounds(q, wo, mr, nc);
-            gv.add(wo, nc, wo, q.tv_off, q.wide, q.rt_off, q.n, q.bp_off, q.n);
+            gv.add(wo, nc, wo, q.mt_off + (int64_t)k1 * nbo, nbo, q.rt_off, q.n, q.bp_off, q.n);
           }
-          U.vsteps.push_back(gv.args(OP_N, OP_N, 1, 0, 0, 0));
+          U.vsteps.push_back(gv.args(OP_N, OP_N, -1, 0, 0, 0));
           U.sdesc.push_back(GjStep{2, k1, k1});
         }
       }
@@ -1055,8 +1047,6 @@ int run_wave(hsc_ctx* h, int ne, const double* E, double eta, const c64* sr, con
       if (sd.kind == 2)   // T R before the trailing product reads it
         GEMM(U.vsteps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es, nullptr, 0);
       GEMM(U.steps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->F, d->aug_es, d->F, d->aug_es);
-      if (sd.kind == 1)   // the virtual rows' update (the deferred rows' transform)
-        GEMM(U.vsteps[st], d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es, d->GJT, d->gjt_es);
       gjup = false;
       tc = keep;
     }
