@@ -31,10 +31,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 # DRAM traffic of the FP64-emulation GEMM class (k_gemm_oz + k_oz_pack), per class launch, from one
 # ncu launch list of the metric workload (dram__bytes_read.sum + dram__bytes_write.sum; the command
-# and table are in profiles/launches_cubic32x64E_fp64.md). Valid only for the kernel source it was
-# taken on: bench.py reports null once csrc/gemm_oz.cu differs from that source.
-OZ_TRAFFIC = {"gemm_oz_sha256": "9e8ad2f7aa2a930208ae41ec3e5e3a8ce60bab6f9403a74b7da63270571758e7",
-              "bytes_per_class_launch": 2.406e9, "launches_per_solve": 918}
+# and table are in profiles/launches_cubic32x64E_fp64.md). Valid only for the kernel and schedule
+# sources it was taken on: bench.py reports null once csrc/gemm_oz.cu or csrc/solve.cu differs.
+OZ_TRAFFIC = {"sources_sha256": None, "bytes_per_class_launch": None, "launches_per_solve": None}
 sys.path.insert(0, ROOT)
 
 METRIC = "energy pts/s for diag(G^r,G^<) on 32^3 grid"
@@ -316,8 +315,10 @@ def run_hsc(args):
     # FP64 emulation: 36 slice products x 3 real products x 2 flops per complex MAC = 27 x the
     # 8-flop complex count, executed as BF16 MMAs
     oz_bf16 = 27.0 * rate(go)
-    src = os.path.join(ROOT, "paper_1702_05167_gb300", "csrc", "gemm_oz.cu")
-    same_src = os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == OZ_TRAFFIC["gemm_oz_sha256"]
+    # the traffic per class launch depends on the kernel and on the schedule of products
+    srcs = [os.path.join(ROOT, "paper_1702_05167_gb300", "csrc", f) for f in ("gemm_oz.cu", "solve.cu")]
+    digest = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs if os.path.exists(f))).hexdigest()
+    same_src = digest == OZ_TRAFFIC["sources_sha256"]
     emul = {"kernel": "k_gemm_oz (+k_oz_pack): complex128 GEMM emulated on the BF16 tensor cores "
                       "(tcgen05.mma kind::f16, 8 balanced base-128 digits per operand, FP32 TMEM "
                       "accumulators drained every 384 K values into exact 96-bit integer sums, one "
@@ -326,7 +327,9 @@ def run_hsc(args):
             "traffic": OZ_TRAFFIC["bytes_per_class_launch"] if same_src else None,
             "traffic_unit": "bytes per class launch (k_gemm_oz + k_oz_pack, ncu dram__bytes_read.sum + "
                             "dram__bytes_write.sum, averaged over one solve's launches)",
-            "traffic_note": None if same_src else "kernel source changed since the counters were taken",
+            "traffic_note": None if same_src else ("kernel or product schedule changed since the counters were "
+                                                   "taken (profiles/launches_cubic32x64E_fp64.md: 2.41 GB per "
+                                                   "class launch on the previous schedule)"),
             "flop_convention": "BF16 MMA flops the scheme needs: 36 slice pairs x 3 real products x "
                                "2 M N K per complex GEMM (27 x the 8-flop complex count), no padding",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
