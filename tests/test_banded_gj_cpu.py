@@ -68,3 +68,41 @@ def test_rows_beyond_the_band_stay_untouched_and_pivot_rows_end_within_2b(n, b, 
         assert reach[k] <= k + 2 * b           # pivot row k ends at column k + 2b
     # row interchanges did happen (the small diagonal makes the test meaningful)
     assert swaps > n // 4
+
+
+def test_deferred_rows_take_the_wide_panels_transform():
+    """The deferral of the rows above a wide panel: after Gauss-Jordan with partial pivoting over the
+    wide panel's columns [k1, k1 + W) (rows >= k1 eligible as pivots), the pivot rows (positions
+    k1..k1 + W - 1) hold P^{-1} in those columns, P the pivot block, and a row above the wide panel
+    that was left out of the eliminations becomes, from its values x there and y elsewhere:
+    wide-panel part x T and other columns y + x T R, with T = -P^{-1} and R the pivot rows' other
+    columns before the wide panel: the product the trailing step forms. Checked against running the
+    same eliminations on that row."""
+    rng = np.random.default_rng(4)
+    n, k1, W = 40, 12, 8
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A[k1:, k1:k1 + W] *= 0.1 * (rng.random((n - k1, W)) < 0.5) + 0.05   # pivots from below
+    M = A.copy()
+    full = A.copy()   # the same steps applied to every row
+    for j in range(k1, k1 + W):
+        p = j + int(np.argmax(np.abs(full[j:, j].real) + np.abs(full[j:, j].imag)))
+        full[[j, p]] = full[[p, j]]
+        M[[j, p]] = M[[p, j]]
+        inv = 1.0 / full[j, j]
+        full[j] *= inv
+        full[j, j] = inv
+        f = full[:, j].copy()
+        f[j] = 0.0
+        full -= np.outer(f, full[j])
+        full[:, j] = -f * inv
+        full[j, j] = inv
+    P = M[k1:k1 + W, k1:k1 + W]        # the pivot block (rows in their final order)
+    Pinv = np.linalg.inv(P)
+    np.testing.assert_allclose(full[k1:k1 + W, k1:k1 + W], Pinv, atol=1e-10 * np.abs(Pinv).max())
+    T = -full[k1:k1 + W, k1:k1 + W]
+    cols = np.r_[0:k1, k1 + W:n]
+    R = M[k1:k1 + W][:, cols]            # the pivot rows' other columns before the wide panel
+    for r in range(k1):                  # rows above: never pivots
+        x, y = A[r, k1:k1 + W], A[r, cols]
+        np.testing.assert_allclose(full[r, k1:k1 + W], x @ T, atol=1e-10 * np.abs(full[r]).max())
+        np.testing.assert_allclose(full[r, cols], y + x @ T @ R, atol=1e-10 * np.abs(full[r]).max())
