@@ -85,3 +85,39 @@ def update_sets(owns, H):
         reach.append({u for u in ext - dom if owner[u] > i})
     return [(np.asarray(own, np.int64), np.array(sorted(r, key=lambda u: (owner[u], u)), dtype=np.int64))
             for own, r in zip(owns, reach)]
+
+
+def selected_general(A, L, clusters):
+    """The same two passes for a general (not complex-symmetric) A, e.g. a Hermitian H with Peierls
+    phases: the LU form, with a left factor beside the right one and column blocks of G beside the
+    row blocks. Upward, per cluster: D^{-1}; X = D^{-1} A_iU; Y = A_Ui D^{-1}; S_UU -= A_Ui X; and
+    the lesser fold L_UU += Y L_ii Y^dagger - Y L_iU - L_Ui Y^dagger (the congruence by the
+    elimination [[I, 0], [-Y, I]], which keeps G^< = A^{-1} L A^{-dagger} on the reduced system).
+    Downward: G_iU = -X G_UU, G_Ui = -G_UU Y, G_ii = D^{-1} - X G_Ui; N_i. = L_i. (G^dagger)_.
+    restricted to i and U; P_iU = D^{-1} N_iU - X P_UU, P_ii = D^{-1} N_ii - X P_Ui with
+    P_Ui = -P_iU^dagger. For a symmetric A, Y = X^T and this is `selected`."""
+    Aw, Lw = A.astype(np.complex128).copy(), L.astype(np.complex128).copy()
+    fac = []
+    for I, U in clusters:
+        Dinv = np.linalg.inv(Aw[np.ix_(I, I)])
+        X = Dinv @ Aw[np.ix_(I, U)]
+        Y = Aw[np.ix_(U, I)] @ Dinv
+        Lii, LiU, LUi = Lw[np.ix_(I, I)].copy(), Lw[np.ix_(I, U)].copy(), Lw[np.ix_(U, I)].copy()
+        if len(U):
+            Aw[np.ix_(U, U)] -= Aw[np.ix_(U, I)] @ X
+            Lw[np.ix_(U, U)] += Y @ Lii @ Y.conj().T - Y @ LiU - LUi @ Y.conj().T
+        fac.append((Dinv, X, Y, Lii, LiU))
+    n = A.shape[0]
+    G = np.zeros((n, n), np.complex128)
+    P = np.zeros((n, n), np.complex128)
+    for (I, U), (Dinv, X, Y, Lii, LiU) in reversed(list(zip(clusters, fac))):
+        Guu, Puu = G[np.ix_(U, U)], P[np.ix_(U, U)]
+        GiU, GUi = -X @ Guu, -Guu @ Y
+        Gii = Dinv - X @ GUi
+        N_ii = Lii @ Gii.conj().T + LiU @ GiU.conj().T
+        N_iU = Lii @ GUi.conj().T + LiU @ Guu.conj().T
+        PiU = Dinv @ N_iU - X @ Puu
+        Pii = Dinv @ N_ii + X @ PiU.conj().T
+        G[np.ix_(I, I)], G[np.ix_(I, U)], G[np.ix_(U, I)] = Gii, GiU, GUi
+        P[np.ix_(I, I)], P[np.ix_(I, U)], P[np.ix_(U, I)] = Pii, PiU, -PiU.conj().T
+    return G, P

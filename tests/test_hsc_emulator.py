@@ -1,6 +1,7 @@
 """The implemented recurrences over the library's own trees reproduce Eqs. 1-2, on the CPU:
 diagonal contacts, DENSE lead self-energies on the top-chain contact clusters, an alternate tree,
-and the graph-ordered G-BN-G stand-in. See hsc_emulator for what this does and does not show."""
+and the graph-ordered G-BN-G stand-in; and the LU form of the recurrences for a Hermitian,
+non-symmetric H (no library solve yet). See hsc_emulator for what this does and does not show."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,35 @@ def test_graph_ordered_gbng_stack():
     G, P, Gd, Pd, _ = _run(dev, 2, -0.8, dense.embed_diag(dev.n, idx, sr[0]),
                            dense.embed_diag(dev.n, idx, sl[0]), geo=False)
     _close(G, P, Gd, Pd, _h_pairs(dev))
+
+
+@pytest.mark.parametrize("phi,E,leaf", [(0.13, 0.4, 2), (0.21, -1.6, 3)])
+def test_lu_form_for_a_hermitian_non_symmetric_h(phi, E, leaf):
+    """A magnetic device (Peierls phases: H Hermitian, H != H^T) on the tree of the same lattice
+    without field (same pattern): the LU form of the recurrences gives G^r and G^< of Eqs. 1-2 on
+    every selected block, while the complex-symmetric recurrences (Y = X^T) do not."""
+    from hsc_emulator import selected_general
+    dims = (7, 5, 4)
+    dev = W.magnetic_cubic_device(dims, phi, seed=7)
+    plain = W.cubic_device(dims, seed=7)
+    Hp, Hm = plain.to_scipy(), dev.to_scipy()
+    assert (abs(Hp) != 0).toarray().tolist() == (abs(Hm) != 0).toarray().tolist()
+    h = _handle(plain, True)
+    st = hsc.hsc_analyze(h, leaf)
+    cl = tree(h, st.n_clusters)
+    hsc.hsc_destroy(h)
+    sr, sl = W.self_energies(dev, 1)
+    idx = dev.contact_unknowns()
+    A = dense.system_matrix(Hm.toarray(), E, ETA, dense.embed_diag(dev.n, idx, sr[0]))
+    Lm = dense.embed_diag(dev.n, idx, sl[0])
+    Gd = dense.retarded(A)
+    Pd = dense.lesser(Gd, Lm)
+    G, P = selected_general(A, Lm, cl)
+    _close(G, P, Gd, Pd, _h_pairs(dev))
+    for I, U in cl:   # the column blocks too
+        if not len(U):
+            continue
+        assert np.abs(G[np.ix_(U, I)] - Gd[np.ix_(U, I)]).max() <= 1e-11 * np.abs(Gd).max()
+        assert np.abs(P[np.ix_(U, I)] - Pd[np.ix_(U, I)]).max() <= 1e-11 * np.abs(Pd).max()
+    Gs, _ = selected(A, Lm, cl)
+    assert np.abs(np.diag(Gs) - np.diag(Gd)).max() > 1e-3 * np.abs(np.diag(Gd)).max()
