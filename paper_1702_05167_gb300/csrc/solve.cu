@@ -29,7 +29,7 @@ namespace hsc {
 struct GemmPair {
   GemmArgs z;    // 64x64 tiles, FP64 tensor pipe (gemm_z)
   GemmArgs tc;   // 128x128 tiles, tcgen05 3xTF32 (gemm_tc)
-  GemmArgs oz;   // 128x64 tiles, FP64 emulation on the BF16 tensor cores (gemm_oz)
+  GemmArgs oz;   // 128x32 tiles, FP64 emulation on the BF16 tensor cores (gemm_oz)
   bool oz_faster = false;   // cost model: the emulation beats the FP64 pipe on this list
 };
 
@@ -219,7 +219,7 @@ constexpr double OZ_TILE = 128 * 32, OZ_DRAIN_DFMA = OZ_TILE * 0.3 * 1.9, OZ_MMA
 struct GemmList {
   std::vector<GemmProb>& all;      // 64x64-tile problem lists
   std::vector<GemmProb>& all128;   // 128x128-tile problem lists
-  std::vector<GemmProb>& alloz;    // 128x64-tile problem lists (FP64 emulation)
+  std::vector<GemmProb>& alloz;    // 128x32-tile problem lists (FP64 emulation)
   size_t start, start128, startoz;
   int tiles = 0, tiles128 = 0, tilesoz = 0;
   int count = 0;
