@@ -511,8 +511,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
             // matrix strides), so A digit s times planes 1..(9 - s) is one MMA of N = 32 (9 - s) <= 256:
             // its column block r lands in the accumulator of diagonal s + r, which starts at TMEM
             // column 32 (s + r - 2). 8 MMAs per K step instead of 36, the same products.
-#pragma unroll
-            // (-Ai) Bi of Re: the instruction descriptor's negate-A bit (BF16 negation is exact)
+            // The product (-Ai) Bi of Re takes the instruction descriptor's negate-A bit (BF16
+            // negation is exact).
             const uint32_t neg = (it.m4 && c == 0 && s >= s0 + it.ks) ? (1u << 13) : 0u;
             for (int si = 0; si < OZ_S; ++si) {
               // the first MMA of a chunk (si = 0) covers every diagonal and starts the accumulation
