@@ -12,8 +12,6 @@ import argparse
 import ctypes
 import time
 
-import numpy as np
-
 
 def main():
     import torch

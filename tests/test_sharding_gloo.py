@@ -4,7 +4,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_1702_05167_gb300 import sharding
 
