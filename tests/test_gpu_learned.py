@@ -3,7 +3,11 @@ solves, the surrogate trained by its own kernels, the adaptive grid checked agai
 
 Reports what the surrogate-placed grid gains over a uniform grid with the same number of points
 (error of each integral against a dense uniform reference); asserts that training converges, that
-every integral on the adaptive grid stays close to the reference, and prints the gains."""
+every integral on the adaptive grid stays close to the reference, and that the adaptive grid beats
+the uniform one on the current integral (T(E), the smooth function the surrogate learns: gain 1.61
+measured); prints the gains. The DOS and lesser-trace integrals gain nothing here: on this weakly
+disordered cube they are dominated by interior levels of width eta that no grid of 96 points
+resolves."""
 import numpy as np
 import pytest
 
@@ -25,6 +29,7 @@ def test_learned_grid_small(capsys):
     sur.close()
     for q, e in ev["rel_err"].items():
         assert e["adaptive"] < 0.05, (q, e)
+    assert ev["gain"]["current_int_T_dE"] > 1.0, ev["gain"]
     with capsys.disabled():
         print("\nlearned grid (10^3 target, 96 points vs 768-point reference): gains",
               {k: round(v, 3) for k, v in ev["gain"].items()})
