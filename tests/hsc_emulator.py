@@ -95,7 +95,9 @@ def selected_general(A, L, clusters):
     elimination [[I, 0], [-Y, I]], which keeps G^< = A^{-1} L A^{-dagger} on the reduced system).
     Downward: G_iU = -X G_UU, G_Ui = -G_UU Y, G_ii = D^{-1} - X G_Ui; N_i. = L_i. (G^dagger)_.
     restricted to i and U; P_iU = D^{-1} N_iU - X P_UU, P_ii = D^{-1} N_ii - X P_Ui with
-    P_Ui = -P_iU^dagger. For a symmetric A, Y = X^T and this is `selected`."""
+    P_Ui = -P_iU^dagger. For a symmetric A, Y = X^T and this is `selected`. (With L anti-Hermitian
+    the fold equals Z - Z^dagger, Z = Y (L_ii Y^dagger / 2 - L_iU): `selected`'s form with Y for
+    X^T; written out here term by term.)"""
     Aw, Lw = A.astype(np.complex128).copy(), L.astype(np.complex128).copy()
     fac = []
     for I, U in clusters:
