@@ -87,7 +87,7 @@ def update_sets(owns, H):
             for own, r in zip(owns, reach)]
 
 
-def selected_general(A, L, clusters):
+def selected_general(A, L, clusters, z_form=False):
     """The same two passes for a general (not complex-symmetric) A, e.g. a Hermitian H with Peierls
     phases: the LU form, with a left factor beside the right one and column blocks of G beside the
     row blocks. Upward, per cluster: D^{-1}; X = D^{-1} A_iU; Y = A_Ui D^{-1}; S_UU -= A_Ui X; and
@@ -97,7 +97,7 @@ def selected_general(A, L, clusters):
     restricted to i and U; P_iU = D^{-1} N_iU - X P_UU, P_ii = D^{-1} N_ii - X P_Ui with
     P_Ui = -P_iU^dagger. For a symmetric A, Y = X^T and this is `selected`. (With L anti-Hermitian
     the fold equals Z - Z^dagger, Z = Y (L_ii Y^dagger / 2 - L_iU): `selected`'s form with Y for
-    X^T; written out here term by term.)"""
+    X^T; written out term by term unless z_form.)"""
     Aw, Lw = A.astype(np.complex128).copy(), L.astype(np.complex128).copy()
     fac = []
     for I, U in clusters:
@@ -107,7 +107,11 @@ def selected_general(A, L, clusters):
         Lii, LiU, LUi = Lw[np.ix_(I, I)].copy(), Lw[np.ix_(I, U)].copy(), Lw[np.ix_(U, I)].copy()
         if len(U):
             Aw[np.ix_(U, U)] -= Aw[np.ix_(U, I)] @ X
-            Lw[np.ix_(U, U)] += Y @ Lii @ Y.conj().T - Y @ LiU - LUi @ Y.conj().T
+            if z_form:
+                Z = Y @ (0.5 * Lii @ Y.conj().T - LiU)
+                Lw[np.ix_(U, U)] += Z - Z.conj().T
+            else:
+                Lw[np.ix_(U, U)] += Y @ Lii @ Y.conj().T - Y @ LiU - LUi @ Y.conj().T
         fac.append((Dinv, X, Y, Lii, LiU))
     n = A.shape[0]
     G = np.zeros((n, n), np.complex128)

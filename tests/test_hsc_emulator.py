@@ -79,11 +79,13 @@ def test_graph_ordered_gbng_stack():
     _close(G, P, Gd, Pd, _h_pairs(dev))
 
 
+@pytest.mark.parametrize("z_form", [False, True])
 @pytest.mark.parametrize("phi,E,leaf", [(0.13, 0.4, 2), (0.21, -1.6, 3)])
-def test_lu_form_for_a_hermitian_non_symmetric_h(phi, E, leaf):
+def test_lu_form_for_a_hermitian_non_symmetric_h(phi, E, leaf, z_form):
     """A magnetic device (Peierls phases: H Hermitian, H != H^T) on the tree of the same lattice
     without field (same pattern): the LU form of the recurrences gives G^r and G^< of Eqs. 1-2 on
-    every selected block, while the complex-symmetric recurrences (Y = X^T) do not."""
+    every selected block, with the lesser fold term by term or as Z - Z^dagger, while the
+    complex-symmetric recurrences (Y = X^T) do not."""
     from hsc_emulator import selected_general
     dims = (7, 5, 4)
     dev = W.magnetic_cubic_device(dims, phi, seed=7)
@@ -100,7 +102,7 @@ def test_lu_form_for_a_hermitian_non_symmetric_h(phi, E, leaf):
     Lm = dense.embed_diag(dev.n, idx, sl[0])
     Gd = dense.retarded(A)
     Pd = dense.lesser(Gd, Lm)
-    G, P = selected_general(A, Lm, cl)
+    G, P = selected_general(A, Lm, cl, z_form)
     _close(G, P, Gd, Pd, _h_pairs(dev))
     for I, U in cl:   # the column blocks too
         if not len(U):
