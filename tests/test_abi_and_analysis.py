@@ -391,3 +391,18 @@ def test_contact_connected_tree_keeps_every_box_on_a_contact_face():
     hsc.hsc_analyze(h, 4)
     assert hsc.hsc_get_option(h, hsc.HSC_OPT_TREE_FORM) == 0
     hsc.hsc_destroy(h)
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/*.h (status codes, precisions, options) has the same value in the
+    Python binding, so a call through either passes the same integer."""
+    consts = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+            for body in re.findall(r"\benum\b[^{]*\{(.*?)\}", txt, flags=re.S):
+                for name, val in re.findall(r"\b(HSC_\w+)\s*=\s*(-?\d+)", body):
+                    consts[name] = int(val)
+    assert {"HSC_OK", "HSC_ERR_TIMEOUT", "HSC_FP64", "HSC_MIXED", "HSC_OPT_LEAF_SPARSE"} <= set(consts)
+    for name, val in consts.items():
+        assert getattr(hsc, name) == val, name
