@@ -406,3 +406,24 @@ def test_binding_constants_match_the_header():
     assert {"HSC_OK", "HSC_ERR_TIMEOUT", "HSC_FP64", "HSC_MIXED", "HSC_OPT_LEAF_SPARSE"} <= set(consts)
     for name, val in consts.items():
         assert getattr(hsc, name) == val, name
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every function the binding declares (ctypes argtypes) takes as many arguments as its
+    prototype in include/*.h: a dropped or extra argument would shift every later one."""
+    protos = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+            txt = re.sub(r"//[^\n]*", "", txt)
+            for name, params in re.findall(r"\b(hsc_\w+)\s*\(([^;{}]*?)\)\s*;", txt, flags=re.S):
+                p = params.strip()
+                protos[name] = 0 if p in ("", "void") else p.count(",") + 1
+    L = hsc.load()
+    checked = 0
+    for name, n in protos.items():
+        at = getattr(L, name).argtypes
+        if at is not None:
+            assert len(at) == n, (name, len(at), n)
+            checked += 1
+    assert checked >= 15
