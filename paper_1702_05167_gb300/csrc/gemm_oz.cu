@@ -23,7 +23,7 @@
 //     memory accumulator, exact for 384 K values (at most 8 pairs: 8 * 65^2 * 384 < 2^24); every
 //     384 K values the 8 accumulators are drained exactly, on the integer pipe (GB300's FP64 pipe
 //     would otherwise bound the kernel), and added to or subtracted from the two 96-bit integers
-//     X 2^63 = H 2^32 + L (int64 H, uint32 L; diagonal d carries the weight 2^(49 - 7 d)) of the
+//     X 2^63 = H 2^32 + L (int64 H, uint32 L; diagonal d carries the weight 2^(63 - 7 d)) of the
 //     complex result's real and imaginary parts (Re = T0 - T1, Im = T2 - T0 - T1, exact);
 //   * for alpha = +-2^a and beta = 0 or +-2^b (real: every product of the solver) the chunks are
 //     added with alpha's sign, beta D / 2^a rounded to the sums' units (2^-63 sigma_i tau_j) is
@@ -610,8 +610,8 @@ k_gemm_oz(GemmArgs g, const uint16_t* slices, int64_t slice_es, const double* sc
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            // weight of diagonal d in X 2^63: 2^(49 - 7 d); the chunk's value is Hc 2^32 + Lc with
-            // b = sum_{d >= 3} v_d 2^(49 - 7 d) (|b| < 2^52.3) split at bit 32
+            // weight of accumulator dg (diagonal dg + 2) in X 2^63: 2^(49 - 7 dg); the chunk is
+            // Hc 2^32 + Lc with b = sum_{dg >= 3} v_dg 2^(49 - 7 dg) (|b| < 2^52.3) split at bit 32
             int x[OZ_ND];
 #pragma unroll
             for (int dg = 0; dg < OZ_ND; ++dg) x[dg] = __float2int_rn(__uint_as_float(r[dg][j]));   // exact
