@@ -33,7 +33,7 @@
 //     alpha, beta (and D beyond 2^31 sigma_i tau_j, a zero scale, a non-finite D) round X and apply
 //     alpha and beta D in FP64; C is written once;
 //   * per K value and real product the error is below 2^-54.5 sigma_i tau_j: 2^-56 from the
-//     truncations (|X_ik| < sigma_i / 2) and 2^-55.2 from the dropped diagonals d >= 10
+//     truncations (|X_ik| < sigma_i / 2) and 2^-55.18 from the dropped diagonals d >= 10
 //     (7 * 64^2 * 2^-70 for d = 10, less beyond); the real part carries two such errors, the
 //     imaginary part three.
 // Pass 1 (k_oz_pack) computes the scales and the slice images: per K step of 16, a 128 x 16 block of
